@@ -1,0 +1,114 @@
+"""Closed forms and quadratures that pin the oracle.
+
+TEST INFRASTRUCTURE ONLY (part of the oracle; see ``oracle/__init__.py``).
+
+Potential of the tilted washboard (Fig. 1): U(phi) = -A cos(phi) - gamma*phi (A = 1 for the
+junction).  For the overdamped Langevin equation phi' = -U'(phi) + sqrt(2 D) xi the mean time to
+advance by one period, from phi0 to phi0 + 2 pi, is independent of phi0 and equals
+
+  T = (1/D) / (1 - exp(-2 pi gamma / D)) * Int_{x0}^{x0+2pi} dx Int_{x-2pi}^{x} exp((U(x)-U(y))/D) dy
+
+(the periodic sum of the left tail replaces the integral from -infinity).  Integrating the
+inner variable over a full period in closed form (Int_0^{2pi} exp(a sin th) dth = 2 pi I0(a))
+gives the one-dimensional Bessel form
+
+  T = (2 pi / D) / (1 - exp(-2 pi gamma / D)) * Int_0^{2pi} exp(-gamma s / D) I0(2 A sin(s/2) / D) ds.
+
+Both are implemented independently (double Gauss-Legendre quadrature vs. one-dimensional
+quadrature of the Bessel form) so that each checks the other.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def barrier(gamma: float, A: float = 1.0) -> float:
+    """Barrier height of U = -A cos phi - gamma phi: 2(sqrt(A^2-gamma^2) - gamma arccos(gamma/A))."""
+    g = gamma / A
+    return 2.0 * A * (math.sqrt(1.0 - g * g) - g * math.acos(g))
+
+
+def _gl_panels(a: float, b: float, panels: int, order: int = 16):
+    """Composite Gauss-Legendre nodes and weights on [a, b]."""
+    xg, wg = np.polynomial.legendre.leggauss(order)
+    edges = np.linspace(a, b, panels + 1)
+    h = np.diff(edges) / 2.0
+    mid = (edges[:-1] + edges[1:]) / 2.0
+    x = (mid[:, None] + h[:, None] * xg[None, :]).ravel()
+    w = (h[:, None] * wg[None, :]).ravel()
+    return x, w
+
+
+def overdamped_mfpt_bessel(gamma: float, D: float, A: float = 1.0, panels: int = 256) -> float:
+    """Mean time to advance one period (2 pi), Bessel form, composite Gauss-Legendre."""
+    from scipy.special import i0e
+    s, w = _gl_panels(0.0, 2.0 * math.pi, panels)
+    a = 2.0 * A * np.sin(s / 2.0) / D
+    # exp(-gamma s / D) I0(a) = i0e(a) * exp(a - gamma s / D)
+    f = i0e(a) * np.exp(a - gamma * s / D)
+    integral = float(np.dot(w, f))
+    return (2.0 * math.pi / D) * integral / (-math.expm1(-2.0 * math.pi * gamma / D))
+
+
+def overdamped_mfpt_double(gamma: float, D: float, A: float = 1.0, x0: float | None = None,
+                           panels: int = 64) -> float:
+    """Mean time from x0 to x0 + 2 pi by direct double quadrature of the integral formula."""
+    if x0 is None:
+        x0 = math.asin(min(gamma / A, 1.0)) if gamma < A else 0.0
+
+    def U(z):
+        return -A * np.cos(z) - gamma * z
+
+    xs, wx = _gl_panels(x0, x0 + 2.0 * math.pi, panels)
+    ss, ws = _gl_panels(0.0, 2.0 * math.pi, panels)
+    # inner: Int_{x-2pi}^{x} exp((U(x)-U(y))/D) dy with y = x - s
+    X = xs[:, None]
+    Y = X - ss[None, :]
+    inner = np.exp((U(X) - U(Y)) / D) @ ws
+    integral = float(np.dot(wx, inner))
+    return (1.0 / D) * integral / (-math.expm1(-2.0 * math.pi * gamma / D))
+
+
+def overdamped_mfpt(gamma: float, D: float, A: float = 1.0, rtol: float = 1e-12) -> float:
+    """Exact overdamped MFPT over one period, converged by doubling the panel count."""
+    panels = 64
+    prev = overdamped_mfpt_bessel(gamma, D, A, panels)
+    while panels < 65536:
+        panels *= 2
+        cur = overdamped_mfpt_bessel(gamma, D, A, panels)
+        if abs(cur - prev) <= rtol * abs(cur):
+            return cur
+        prev = cur
+    return prev
+
+
+def kramers_overdamped(gamma: float, D: float) -> float:
+    """Kramers' high-barrier limit for the tilted washboard (A = 1):
+    2 pi / sqrt(U''(min) |U''(max)|) * exp(dU/D) = 2 pi / sqrt(1 - gamma^2) * exp(dU/D)."""
+    return 2.0 * math.pi / math.sqrt(1.0 - gamma * gamma) * math.exp(barrier(gamma) / D)
+
+
+def running_period(gamma: float) -> float:
+    """Noise-free overdamped period for gamma > 1: Int_0^{2pi} dphi / (gamma - sin phi)."""
+    return 2.0 * math.pi / math.sqrt(gamma * gamma - 1.0)
+
+
+def inverse_gaussian(L: float, drift: float, D: float):
+    """First passage of phi' = drift + sqrt(2D) xi over a distance L (sin term absent):
+    inverse Gaussian with mean L/drift and shape L^2 / (2D).  Returns a frozen scipy law."""
+    from scipy import stats as _st
+    mean = L / drift
+    shape = L * L / (2.0 * D)
+    return _st.invgauss(mean / shape, scale=shape)
+
+
+def slow_passage_delay(nu: float) -> float:
+    """Noise-free overdamped ramp through the saddle-node at gamma = 1: near phi = pi/2,
+    x' = (gamma - 1) + x^2 / 2 with gamma - 1 = nu t; rescaling to y' = s + y^2 puts the
+    blow-up at s = |a1| (first zero of the Airy function Ai), so the bias at switching exceeds
+    1 by 2^(1/3) |a1| nu^(2/3) to leading order."""
+    from scipy.special import ai_zeros
+    a1 = abs(float(ai_zeros(1)[0][0]))
+    return 2.0 ** (1.0 / 3.0) * a1 * nu ** (2.0 / 3.0)
