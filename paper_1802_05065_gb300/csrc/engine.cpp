@@ -1,0 +1,758 @@
+// engine.cpp -- host side of the persistent batched FPT engine and its C ABI.
+//
+// One engine iteration:
+//   1. admission: queued requests take a free slot when their device memory fits the budget;
+//      their decoded constants (Alg. 1 lines 4-7, Alg. 3 lines 5-9) are copied into the slot
+//      table and their accumulators are zeroed;
+//   2. the claimable-slot lists and fair-share caps are refreshed (pinned host -> device);
+//   3. one resident-kernel launch advances every lane by up to chunk_steps steps;
+//   4. the scan kernel folds completed id blocks and applies the stop rule;
+//   5. the per-slot status and counters come back to pinned host memory.
+// Steps 2-5 are one CUDA graph.  Slots are reused only after no lane holds a trajectory of the
+// old request (its in-flight count has reached zero).
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "engine_dev.h"
+#include "internal.h"
+
+namespace fpt {
+cudaError_t launch_engine_chunk(const EngineDev &E, int T, unsigned grid, unsigned block,
+                                cudaStream_t s);
+cudaError_t launch_engine_scan(const EngineDev &E, cudaStream_t s);
+cudaError_t engine_chunk_occupancy(int T, int block, int *blocks_per_sm);
+}  // namespace fpt
+
+using namespace fpt;
+using Clock = std::chrono::steady_clock;
+
+namespace {
+
+enum Phase { kPending, kRunning, kFinished, kCancelled };
+
+struct Request {
+    uint64_t id = 0;
+    fpt_params params{};
+    Decoded dec;
+    uint64_t n_traj = 0, seed = 0;
+    int slot = -1;
+    Phase phase = kPending;
+    bool released = false;
+    IdBlockAcc *acc = nullptr;
+    unsigned *hist = nullptr;
+    long long *per_traj = nullptr;
+    size_t bytes = 0;
+    uint32_t stop_block = 4096, n_idblocks = 0;
+    unsigned prefix = 0;
+    fpt_sums sums{};
+    fpt_result result{};
+    Clock::time_point t_submit;
+};
+
+size_t request_bytes(const fpt_params &p, uint64_t n_traj, uint32_t B) {
+    const uint64_t nb = (n_traj + B - 1) / B;
+    size_t bytes = nb * sizeof(IdBlockAcc) + nb * static_cast<size_t>(p.hist_bins) * 4;
+    if (p.keep_per_traj) bytes += n_traj * 8;
+    return bytes;
+}
+
+}  // namespace
+
+struct fpt_engine {
+    fpt_engine_config cfg{};
+    int device = 0;
+    cudaStream_t stream = nullptr, io = nullptr;
+    bool own_stream = false;
+    int sms = 0, grid = 0, block = 256, T = 2, maxr = 256;
+    unsigned lanes = 0, chunk_blocks = 0;
+    // device
+    SlotDev *d_slots = nullptr;
+    SlotCtl *d_ctl = nullptr;
+    int *d_caps = nullptr, *d_act = nullptr, *d_act_count = nullptr;
+    void *d_lane_mem = nullptr;
+    int *d_warp_kind = nullptr;
+    unsigned *d_warp_cursor = nullptr;
+    unsigned long long *d_counters = nullptr;
+    EngineDev dev{};
+    // pinned host
+    SlotDev *h_slots = nullptr;
+    SlotCtl *h_ctl = nullptr, *h_ctl_init = nullptr;
+    int *h_caps = nullptr, *h_act = nullptr, *h_act_count = nullptr;
+    unsigned long long *h_counters = nullptr;
+    int *h_state = nullptr;
+    // resident-kernel timing (events around the chunk kernel, recorded inside the graph)
+    cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;
+    double kernel_ms = 0.0;
+    bool capturing = false;
+    // graph
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    // bookkeeping
+    std::mutex mu, drive_mu;
+    std::condition_variable cv_work, cv_done;
+    std::thread service;
+    bool stop = false;
+    std::deque<uint64_t> pending;
+    std::map<uint64_t, std::unique_ptr<Request>> reqs;
+    std::vector<uint64_t> slot_req;
+    uint64_t next_id = 1;
+    uint64_t budget = 0, mem_used = 0;
+    uint64_t iterations = 0;
+    bool broken = false;
+    std::string error;
+};
+
+namespace {
+
+thread_local std::string t_engine_error;
+
+fpt_status fail(fpt_engine *e, fpt_status st, const std::string &m) {
+    if (e) {
+        e->error = m;
+        t_engine_error = m;
+    } else {
+        set_error(m);
+    }
+    return st;
+}
+
+#define CK(call)                                                                         \
+    do {                                                                                 \
+        cudaError_t _e = (call);                                                         \
+        if (_e != cudaSuccess) {                                                         \
+            e->broken = true;                                                            \
+            return fail(e, FPT_ECUDA, std::string(#call) + ": " + cudaGetErrorString(_e)); \
+        }                                                                                \
+    } while (0)
+
+void free_request_buffers(Request &R, fpt_engine *e) {
+    if (R.acc) cudaFree(R.acc);
+    if (R.hist) cudaFree(R.hist);
+    if (R.per_traj) cudaFree(R.per_traj);
+    R.acc = nullptr;
+    R.hist = nullptr;
+    R.per_traj = nullptr;
+    e->mem_used -= R.bytes;
+    R.bytes = 0;
+}
+
+// Admit queued requests (called with mu held, on the driving thread).
+fpt_status admit(fpt_engine *e) {
+    for (auto it = e->pending.begin(); it != e->pending.end();) {
+        Request &R = *e->reqs[*it];
+        if (R.released) {
+            it = e->pending.erase(it);
+            e->reqs.erase(R.id);
+            continue;
+        }
+        int s = -1;
+        for (int i = 0; i < e->maxr; ++i)
+            if (e->slot_req[i] == 0) {
+                s = i;
+                break;
+            }
+        if (s < 0) break;
+        const size_t bytes = request_bytes(R.params, R.n_traj, R.stop_block);
+        if (e->mem_used + bytes > e->budget) {
+            ++it;
+            continue;
+        }
+        const uint64_t nb = R.n_idblocks;
+        CK(cudaMalloc(&R.acc, nb * sizeof(IdBlockAcc)));
+        CK(cudaMalloc(&R.hist, nb * static_cast<size_t>(R.params.hist_bins) * 4));
+        CK(cudaMemsetAsync(R.acc, 0, nb * sizeof(IdBlockAcc), e->stream));
+        CK(cudaMemsetAsync(R.hist, 0, nb * static_cast<size_t>(R.params.hist_bins) * 4, e->stream));
+        if (R.params.keep_per_traj) {
+            CK(cudaMalloc(&R.per_traj, R.n_traj * 8));
+            CK(cudaMemsetAsync(R.per_traj, 0xFF, R.n_traj * 8, e->stream));
+        }
+        R.bytes = bytes;
+        e->mem_used += bytes;
+        const Decoded &d = R.dec;
+        SlotDev &S = e->h_slots[s];
+        std::memset(&S, 0, sizeof(S));
+        S.dt = d.dt_f;
+        S.A = d.A_f;
+        S.amp = d.amp_f;
+        S.bmc = d.bmc_f;
+        S.nudt = d.nudt_f;
+        S.v0 = d.v0_f;
+        S.r0 = d.r0_f;
+        S.eb0 = d.eb0_f;
+        S.w0 = d.w0;
+        S.model = d.model;
+        S.key0 = static_cast<uint32_t>(R.seed);
+        S.key1 = static_cast<uint32_t>(R.seed >> 32);
+        S.traj_offset = R.params.traj_offset;
+        S.n_traj = R.n_traj;
+        S.max_steps = d.max_steps;
+        S.nblocks = (d.max_steps + 3) / 4;
+        S.gamma0 = d.gamma0;
+        S.nudt_d = d.nudt;
+        S.output = d.output;
+        S.hist_bins = d.hist_bins;
+        S.out_a = d.out_a;
+        S.out_b = d.out_b;
+        S.hist_lo = d.hist_lo;
+        S.hist_hi = d.hist_hi;
+        S.hist_inv_w = d.hist_inv_w;
+        S.stop_rse = R.params.stop_rse;
+        S.stop_block = R.stop_block;
+        S.n_idblocks = R.n_idblocks;
+        S.acc = R.acc;
+        S.hist = R.hist;
+        S.per_traj = R.per_traj;
+        CK(cudaMemcpyAsync(e->d_slots + s, &S, sizeof(SlotDev), cudaMemcpyHostToDevice, e->stream));
+        SlotCtl &C = e->h_ctl_init[s];
+        std::memset(&C, 0, sizeof(C));
+        C.state = kSlotActive;
+        CK(cudaMemcpyAsync(e->d_ctl + s, &C, sizeof(SlotCtl), cudaMemcpyHostToDevice, e->stream));
+        e->slot_req[s] = R.id;
+        R.slot = s;
+        R.phase = kRunning;
+        it = e->pending.erase(it);
+    }
+    return FPT_OK;
+}
+
+void build_lists(fpt_engine *e) {
+    int cnt[2] = {0, 0};
+    int active = 0;
+    for (int s = 0; s < e->maxr; ++s) {
+        if (!e->slot_req[s]) continue;
+        Request &R = *e->reqs[e->slot_req[s]];
+        if (R.phase != kRunning) continue;
+        e->h_act[R.dec.model * e->maxr + cnt[R.dec.model]++] = s;
+        ++active;
+    }
+    e->h_act_count[0] = cnt[0];
+    e->h_act_count[1] = cnt[1];
+    const int cap = active ? static_cast<int>((e->lanes + active - 1) / active) + 32 : 0;
+    for (int s = 0; s < e->maxr; ++s) e->h_caps[s] = cap;
+}
+
+fpt_status enqueue_iteration(fpt_engine *e) {
+    if (e->exec) {
+        CK(cudaGraphLaunch(e->exec, e->stream));
+        return FPT_OK;
+    }
+    CK(cudaMemcpyAsync(e->d_caps, e->h_caps, e->maxr * sizeof(int), cudaMemcpyHostToDevice, e->stream));
+    CK(cudaMemcpyAsync(e->d_act, e->h_act, 2 * e->maxr * sizeof(int), cudaMemcpyHostToDevice, e->stream));
+    CK(cudaMemcpyAsync(e->d_act_count, e->h_act_count, 2 * sizeof(int), cudaMemcpyHostToDevice, e->stream));
+    const unsigned evflags = e->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    CK(cudaEventRecordWithFlags(e->ev_k0, e->stream, evflags));
+    CK(launch_engine_chunk(e->dev, e->T, e->grid, e->block, e->stream));
+    CK(cudaEventRecordWithFlags(e->ev_k1, e->stream, evflags));
+    CK(launch_engine_scan(e->dev, e->stream));
+    CK(cudaMemcpyAsync(e->h_ctl, e->d_ctl, e->maxr * sizeof(SlotCtl), cudaMemcpyDeviceToHost, e->stream));
+    CK(cudaMemcpyAsync(e->h_counters, e->d_counters, kCntCount * sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, e->stream));
+    return FPT_OK;
+}
+
+void finalize(fpt_engine *e, Request &R, const SlotCtl &C) {
+    R.prefix = C.prefix;
+    R.sums.n_done = C.n_done;
+    R.sums.n_escaped = C.n_esc;
+    R.sums.s1_lo = C.s1_lo;
+    R.sums.s1_hi = C.s1_hi;
+    R.sums.s2_lo = C.s2_lo;
+    R.sums.s2_hi = C.s2_hi;
+    R.sums.under = C.under;
+    R.sums.over = C.over;
+    std::memset(&R.result, 0, sizeof(R.result));
+    R.result.state = FPT_OK;
+    R.result.n_used = C.n_done;
+    sums_to_result(R.dec, R.sums, &R.result);
+    const unsigned __int128 s1 = (static_cast<unsigned __int128>(C.s1_hi) << 64) | C.s1_lo;
+    const unsigned __int128 tot =
+        s1 + static_cast<unsigned __int128>(C.n_done - C.n_esc) * R.dec.max_steps;
+    R.result.steps_total = (tot >> 64) ? UINT64_MAX : static_cast<uint64_t>(tot);
+    R.result.latency_s = std::chrono::duration<double>(Clock::now() - R.t_submit).count();
+    (void)e;
+}
+
+// Read the status of the last iteration (mu held).
+void process_status(fpt_engine *e) {
+    for (int s = 0; s < e->maxr; ++s) {
+        if (!e->slot_req[s]) continue;
+        Request &R = *e->reqs[e->slot_req[s]];
+        const SlotCtl &C = e->h_ctl[s];
+        if (R.phase == kRunning && C.state == kSlotFinished) {
+            finalize(e, R, C);
+            R.phase = kFinished;
+        }
+        if ((R.phase == kFinished || R.phase == kCancelled) && C.state != kSlotActive &&
+            C.inflight == 0) {
+            e->slot_req[s] = 0;
+            R.slot = -1;
+            if (R.released) {
+                free_request_buffers(R, e);
+                e->reqs.erase(R.id);
+            }
+        }
+    }
+}
+
+fpt_status iteration(fpt_engine *e) {
+    if (e->broken) return fail(e, FPT_ECUDA, "engine is in an error state: " + e->error);
+    {
+        std::lock_guard<std::mutex> lk(e->mu);
+        fpt_status st = admit(e);
+        if (st != FPT_OK) return st;
+        build_lists(e);
+    }
+    fpt_status st = enqueue_iteration(e);
+    if (st != FPT_OK) return st;
+    CK(cudaStreamSynchronize(e->stream));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, e->ev_k0, e->ev_k1));
+    {
+        std::lock_guard<std::mutex> lk(e->mu);
+        process_status(e);
+        ++e->iterations;
+        e->kernel_ms += ms;
+    }
+    e->cv_done.notify_all();
+    return FPT_OK;
+}
+
+bool has_work(fpt_engine *e) {
+    if (!e->pending.empty()) return true;
+    for (int s = 0; s < e->maxr; ++s)
+        if (e->slot_req[s]) return true;
+    return false;
+}
+
+void service_loop(fpt_engine *e) {
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(e->mu);
+            e->cv_work.wait(lk, [&] { return e->stop || has_work(e); });
+            if (e->stop) return;
+        }
+        std::lock_guard<std::mutex> dk(e->drive_mu);
+        if (iteration(e) != FPT_OK) {
+            e->cv_done.notify_all();
+            return;
+        }
+    }
+}
+
+fpt_status capture_graph(fpt_engine *e) {
+    CK(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
+    fpt_status st = FPT_OK;
+    {
+        e->exec = nullptr;
+        e->capturing = true;
+        st = enqueue_iteration(e);
+        e->capturing = false;
+    }
+    cudaGraph_t g = nullptr;
+    const cudaError_t ce = cudaStreamEndCapture(e->stream, &g);
+    if (st != FPT_OK) return st;
+    CK(ce);
+    e->graph = g;
+    CK(cudaGraphInstantiate(&e->exec, e->graph, 0));
+    return FPT_OK;
+}
+
+void destroy_all(fpt_engine *e) {
+    if (e->service.joinable()) {
+        {
+            std::lock_guard<std::mutex> lk(e->mu);
+            e->stop = true;
+        }
+        e->cv_work.notify_all();
+        e->service.join();
+    }
+    cudaSetDevice(e->device);
+    if (e->stream) cudaStreamSynchronize(e->stream);
+    for (auto &kv : e->reqs) free_request_buffers(*kv.second, e);
+    e->reqs.clear();
+    if (e->exec) cudaGraphExecDestroy(e->exec);
+    if (e->graph) cudaGraphDestroy(e->graph);
+    cudaFree(e->d_slots);
+    cudaFree(e->d_ctl);
+    cudaFree(e->d_caps);
+    cudaFree(e->d_act);
+    cudaFree(e->d_act_count);
+    cudaFree(e->d_lane_mem);
+    cudaFree(e->d_warp_kind);
+    cudaFree(e->d_warp_cursor);
+    cudaFree(e->d_counters);
+    cudaFreeHost(e->h_slots);
+    cudaFreeHost(e->h_ctl);
+    cudaFreeHost(e->h_ctl_init);
+    cudaFreeHost(e->h_caps);
+    cudaFreeHost(e->h_act);
+    cudaFreeHost(e->h_act_count);
+    cudaFreeHost(e->h_counters);
+    if (e->ev_k0) cudaEventDestroy(e->ev_k0);
+    if (e->ev_k1) cudaEventDestroy(e->ev_k1);
+    if (e->io) cudaStreamDestroy(e->io);
+    if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
+}
+
+fpt_status create_impl(const fpt_engine_config *cfg_in, fpt_engine *e) {
+    fpt_engine_config cfg{};
+    if (cfg_in) cfg = *cfg_in;
+    else cfg.use_graph = 1;
+    e->cfg = cfg;
+    e->device = cfg.device;
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (cfg.device < 0 || cfg.device >= ndev) return fail(e, FPT_EINVAL, "bad device ordinal");
+    CK(cudaSetDevice(cfg.device));
+    e->maxr = cfg.max_requests > 0 ? cfg.max_requests : 256;
+    if (e->maxr > 1024) return fail(e, FPT_EINVAL, "max_requests must be <= 1024");
+    e->block = cfg.threads_per_block > 0 ? cfg.threads_per_block : 256;
+    if (e->block % 32 || e->block > 256) return fail(e, FPT_EINVAL, "threads_per_block: multiple of 32, <= 256");
+    e->T = cfg.traj_per_thread > 0 ? cfg.traj_per_thread : 2;
+    if (e->T != 1 && e->T != 2) return fail(e, FPT_EINVAL, "traj_per_thread must be 1 or 2");
+    const uint32_t chunk = cfg.chunk_steps ? cfg.chunk_steps : 16384;
+    if (chunk % 4 || chunk > (1u << 24)) return fail(e, FPT_EINVAL, "chunk_steps: multiple of 4, <= 2^24");
+    e->chunk_blocks = chunk / 4;
+    CK(cudaDeviceGetAttribute(&e->sms, cudaDevAttrMultiProcessorCount, cfg.device));
+    int bps = 0;
+    CK(engine_chunk_occupancy(e->T, e->block, &bps));
+    if (bps < 1) return fail(e, FPT_ECUDA, "resident kernel does not fit on an SM");
+    if (cfg.blocks_per_sm > 0) bps = std::min(bps, cfg.blocks_per_sm);
+    e->grid = e->sms * bps;
+    e->lanes = static_cast<unsigned>(e->grid) * e->block * e->T;
+    size_t free_b = 0, total_b = 0;
+    CK(cudaMemGetInfo(&free_b, &total_b));
+    e->budget = cfg.mem_budget_bytes ? cfg.mem_budget_bytes : free_b / 4;
+    if (cfg.stream) {
+        e->stream = static_cast<cudaStream_t>(cfg.stream);
+    } else {
+        CK(cudaStreamCreateWithFlags(&e->stream, cudaStreamNonBlocking));
+        e->own_stream = true;
+    }
+    CK(cudaStreamCreateWithFlags(&e->io, cudaStreamNonBlocking));
+    CK(cudaEventCreate(&e->ev_k0));
+    CK(cudaEventCreate(&e->ev_k1));
+    const int R = e->maxr;
+    CK(cudaMalloc(&e->d_slots, R * sizeof(SlotDev)));
+    CK(cudaMalloc(&e->d_ctl, R * sizeof(SlotCtl)));
+    CK(cudaMalloc(&e->d_caps, R * sizeof(int)));
+    CK(cudaMalloc(&e->d_act, 2 * R * sizeof(int)));
+    CK(cudaMalloc(&e->d_act_count, 2 * sizeof(int)));
+    const size_t L = e->lanes;
+    CK(cudaMalloc(&e->d_lane_mem, L * 4 * 10));
+    const unsigned nwarps = static_cast<unsigned>(e->grid) * e->block / 32;
+    CK(cudaMalloc(&e->d_warp_kind, nwarps * sizeof(int)));
+    CK(cudaMalloc(&e->d_warp_cursor, nwarps * sizeof(unsigned)));
+    CK(cudaMalloc(&e->d_counters, kCntCount * sizeof(unsigned long long)));
+    CK(cudaMemsetAsync(e->d_ctl, 0, R * sizeof(SlotCtl), e->stream));
+    CK(cudaMemsetAsync(e->d_lane_mem, 0, L * 4 * 10, e->stream));
+    char *m = static_cast<char *>(e->d_lane_mem);
+    LaneSoA &ls = e->dev.lanes;
+    ls.r = reinterpret_cast<float *>(m + 0 * L * 4);
+    ls.v = reinterpret_cast<float *>(m + 1 * L * 4);
+    ls.hb = reinterpret_cast<float *>(m + 2 * L * 4);
+    ls.w = reinterpret_cast<int *>(m + 3 * L * 4);
+    ls.slot = reinterpret_cast<int *>(m + 4 * L * 4);
+    ls.c_lo = reinterpret_cast<unsigned *>(m + 5 * L * 4);
+    ls.c_hi = reinterpret_cast<unsigned *>(m + 6 * L * 4);
+    ls.gid_lo = reinterpret_cast<unsigned *>(m + 7 * L * 4);
+    ls.gid_hi = reinterpret_cast<unsigned *>(m + 8 * L * 4);
+    ls.budget = reinterpret_cast<unsigned *>(m + 9 * L * 4);
+    CK(cudaMemsetAsync(ls.slot, 0xFF, L * 4, e->stream));
+    CK(cudaMemsetAsync(e->d_warp_kind, 0xFF, nwarps * sizeof(int), e->stream));
+    CK(cudaMemsetAsync(e->d_warp_cursor, 0, nwarps * sizeof(unsigned), e->stream));
+    CK(cudaMemsetAsync(e->d_counters, 0, kCntCount * sizeof(unsigned long long), e->stream));
+    CK(cudaMallocHost(&e->h_slots, R * sizeof(SlotDev)));
+    CK(cudaMallocHost(&e->h_ctl, R * sizeof(SlotCtl)));
+    CK(cudaMallocHost(&e->h_ctl_init, R * sizeof(SlotCtl)));
+    CK(cudaMallocHost(&e->h_caps, R * sizeof(int)));
+    CK(cudaMallocHost(&e->h_act, 2 * R * sizeof(int)));
+    CK(cudaMallocHost(&e->h_act_count, 2 * sizeof(int)));
+    CK(cudaMallocHost(&e->h_counters, kCntCount * sizeof(unsigned long long)));
+    std::memset(e->h_ctl, 0, R * sizeof(SlotCtl));
+    std::memset(e->h_caps, 0, R * sizeof(int));
+    std::memset(e->h_act, 0, 2 * R * sizeof(int));
+    std::memset(e->h_act_count, 0, 2 * sizeof(int));
+    std::memset(e->h_counters, 0, kCntCount * sizeof(unsigned long long));
+    e->slot_req.assign(R, 0);
+    EngineDev &d = e->dev;
+    d.slots = e->d_slots;
+    d.ctl = e->d_ctl;
+    d.caps = e->d_caps;
+    d.act_list = e->d_act;
+    d.act_count = e->d_act_count;
+    d.warp_kind = e->d_warp_kind;
+    d.warp_cursor = e->d_warp_cursor;
+    d.counters = e->d_counters;
+    d.chunk_blocks = e->chunk_blocks;
+    d.max_requests = R;
+    CK(cudaStreamSynchronize(e->stream));
+    if (cfg.use_graph) {
+        fpt_status st = capture_graph(e);
+        if (st != FPT_OK) return st;
+    }
+    if (cfg.service_thread) e->service = std::thread(service_loop, e);
+    return FPT_OK;
+}
+
+Request *find(fpt_engine *e, uint64_t id) {
+    auto it = e->reqs.find(id);
+    if (it == e->reqs.end() || it->second->released) return nullptr;
+    return it->second.get();
+}
+
+}  // namespace
+
+extern "C" fpt_status fpt_create(const fpt_engine_config *config, fpt_engine **out) {
+    if (!out) return fail(nullptr, FPT_EINVAL, "out is NULL");
+    *out = nullptr;
+    auto *e = new (std::nothrow) fpt_engine();
+    if (!e) return fail(nullptr, FPT_ENOMEM, "host allocation failed");
+    const fpt_status st = create_impl(config, e);
+    if (st != FPT_OK) {
+        set_error(e->error);
+        destroy_all(e);
+        delete e;
+        return st;
+    }
+    *out = e;
+    return FPT_OK;
+}
+
+extern "C" fpt_status fpt_submit(fpt_engine *e, const fpt_params *params, uint64_t n_traj,
+                                 uint64_t seed, uint64_t *req_id) {
+    if (!e || !params || !req_id) return fail(e, FPT_EINVAL, "NULL argument");
+    auto R = std::make_unique<Request>();
+    std::string err;
+    if (!decode(params, &R->dec, &err)) return fail(e, FPT_EINVAL, err);
+    if (params->precision != FPT_FP32)
+        return fail(e, FPT_EINVAL, "the engine integrates FP32; use fpt_plain_launch for FP64");
+    if (n_traj < 1 || n_traj > (1ull << 40)) return fail(e, FPT_EINVAL, "n_traj must be in [1, 2^40]");
+    R->params = *params;
+    R->n_traj = n_traj;
+    R->seed = seed;
+    R->stop_block = params->stop_block ? params->stop_block : 4096;
+    const uint64_t nb = (n_traj + R->stop_block - 1) / R->stop_block;
+    if (nb > 0xFFFFFFFFull) return fail(e, FPT_EINVAL, "too many id blocks");
+    R->n_idblocks = static_cast<uint32_t>(nb);
+    if (request_bytes(*params, n_traj, R->stop_block) > e->budget)
+        return fail(e, FPT_ENOMEM, "request larger than the engine's memory budget");
+    R->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(e->mu);
+        if (e->broken) return fail(e, FPT_ECUDA, "engine is in an error state: " + e->error);
+        if (e->pending.size() >= (1u << 20)) return fail(e, FPT_EFULL, "submission queue full");
+        R->id = e->next_id++;
+        *req_id = R->id;
+        e->pending.push_back(R->id);
+        e->reqs[R->id] = std::move(R);
+    }
+    e->cv_work.notify_all();
+    return FPT_OK;
+}
+
+extern "C" fpt_status fpt_step(fpt_engine *e, int n_iterations) {
+    if (!e) return fail(e, FPT_EINVAL, "NULL engine");
+    if (e->cfg.service_thread) return fail(e, FPT_EBUSY, "a service thread drives this engine");
+    std::lock_guard<std::mutex> dk(e->drive_mu);
+    CK(cudaSetDevice(e->device));
+    for (int i = 0; i < n_iterations; ++i) {
+        const fpt_status st = iteration(e);
+        if (st != FPT_OK) return st;
+    }
+    return FPT_OK;
+}
+
+extern "C" fpt_status fpt_poll(fpt_engine *e, uint64_t req_id, fpt_result *out) {
+    if (!e || !out) return fail(e, FPT_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(e->mu);
+    Request *R = find(e, req_id);
+    if (!R) return fail(e, FPT_ENOTFOUND, "unknown request id");
+    if (R->phase == kFinished) {
+        *out = R->result;
+        return FPT_OK;
+    }
+    std::memset(out, 0, sizeof(*out));
+    out->state = FPT_PENDING;
+    if (R->slot >= 0) {
+        const SlotCtl &C = e->h_ctl[R->slot];
+        out->n_used = C.n_done;
+        out->n_escaped = C.n_esc;
+        out->n_censored = C.n_done - C.n_esc;
+    }
+    out->latency_s = std::chrono::duration<double>(Clock::now() - R->t_submit).count();
+    if (e->broken) return fail(e, FPT_ECUDA, "engine is in an error state: " + e->error);
+    return FPT_PENDING;
+}
+
+extern "C" fpt_status fpt_wait(fpt_engine *e, uint64_t req_id, double timeout_s, fpt_result *out) {
+    if (!e || !out) return fail(e, FPT_EINVAL, "NULL argument");
+    const auto deadline = Clock::now() + std::chrono::duration_cast<Clock::duration>(
+                                             std::chrono::duration<double>(timeout_s));
+    for (;;) {
+        {
+            std::unique_lock<std::mutex> lk(e->mu);
+            Request *R = find(e, req_id);
+            if (!R) return fail(e, FPT_ENOTFOUND, "unknown request id");
+            if (R->phase == kFinished) {
+                *out = R->result;
+                return FPT_OK;
+            }
+            if (e->broken) return fail(e, FPT_ECUDA, "engine is in an error state: " + e->error);
+            if (Clock::now() >= deadline) return fail(e, FPT_ETIMEDOUT, "timed out");
+            if (e->cfg.service_thread) {
+                e->cv_done.wait_until(lk, deadline);
+                continue;
+            }
+        }
+        std::lock_guard<std::mutex> dk(e->drive_mu);
+        cudaSetDevice(e->device);
+        const fpt_status st = iteration(e);
+        if (st != FPT_OK) return st;
+    }
+}
+
+extern "C" fpt_status fpt_histogram(fpt_engine *e, uint64_t req_id, uint64_t *counts, int nbins,
+                                    uint64_t *under, uint64_t *over) {
+    if (!e || !counts) return fail(e, FPT_EINVAL, "NULL argument");
+    unsigned prefix;
+    unsigned *hist;
+    {
+        std::lock_guard<std::mutex> lk(e->mu);
+        Request *R = find(e, req_id);
+        if (!R) return fail(e, FPT_ENOTFOUND, "unknown request id");
+        if (R->phase != kFinished) return fail(e, FPT_PENDING, "request not finished");
+        if (nbins != R->params.hist_bins) return fail(e, FPT_EINVAL, "nbins != params.hist_bins");
+        prefix = R->prefix;
+        hist = R->hist;
+        if (under) *under = R->sums.under;
+        if (over) *over = R->sums.over;
+    }
+    std::vector<unsigned> rows(static_cast<size_t>(prefix) * nbins);
+    CK(cudaSetDevice(e->device));
+    if (!rows.empty()) {
+        CK(cudaMemcpyAsync(rows.data(), hist, rows.size() * 4, cudaMemcpyDeviceToHost, e->io));
+        CK(cudaStreamSynchronize(e->io));
+    }
+    std::fill(counts, counts + nbins, 0ull);
+    for (unsigned p = 0; p < prefix; ++p)
+        for (int b = 0; b < nbins; ++b) counts[b] += rows[static_cast<size_t>(p) * nbins + b];
+    return FPT_OK;
+}
+
+static fpt_status per_traj_impl(fpt_engine *e, uint64_t req_id, int64_t *steps, double *xs,
+                                uint64_t n) {
+    long long *src;
+    Decoded d;
+    {
+        std::lock_guard<std::mutex> lk(e->mu);
+        Request *R = find(e, req_id);
+        if (!R) return fail(e, FPT_ENOTFOUND, "unknown request id");
+        if (R->phase != kFinished) return fail(e, FPT_PENDING, "request not finished");
+        if (!R->per_traj) return fail(e, FPT_EINVAL, "request was submitted without keep_per_traj");
+        if (n > R->n_traj) return fail(e, FPT_EINVAL, "n exceeds n_traj");
+        src = R->per_traj;
+        d = R->dec;
+    }
+    std::vector<int64_t> tmp;
+    int64_t *dst = steps;
+    if (!dst) {
+        tmp.resize(n);
+        dst = tmp.data();
+    }
+    CK(cudaSetDevice(e->device));
+    if (n) {
+        CK(cudaMemcpyAsync(dst, src, n * 8, cudaMemcpyDeviceToHost, e->io));
+        CK(cudaStreamSynchronize(e->io));
+    }
+    if (xs)
+        for (uint64_t i = 0; i < n; ++i)
+            xs[i] = dst[i] < 0 ? (d.output == FPT_OUT_TIME ? -1.0 : NAN)
+                               : observable(d, static_cast<uint64_t>(dst[i]));
+    return FPT_OK;
+}
+
+extern "C" fpt_status fpt_per_traj(fpt_engine *e, uint64_t req_id, double *out, uint64_t n) {
+    if (!e || (!out && n)) return fail(e, FPT_EINVAL, "NULL argument");
+    return per_traj_impl(e, req_id, nullptr, out, n);
+}
+
+extern "C" fpt_status fpt_per_traj_steps(fpt_engine *e, uint64_t req_id, int64_t *out, uint64_t n) {
+    if (!e || (!out && n)) return fail(e, FPT_EINVAL, "NULL argument");
+    return per_traj_impl(e, req_id, out, nullptr, n);
+}
+
+extern "C" fpt_status fpt_release(fpt_engine *e, uint64_t req_id) {
+    if (!e) return fail(e, FPT_EINVAL, "NULL engine");
+    std::lock_guard<std::mutex> lk(e->mu);
+    Request *R = find(e, req_id);
+    if (!R) return fail(e, FPT_ENOTFOUND, "unknown request id");
+    R->released = true;
+    if (R->phase == kPending) {
+        e->pending.erase(std::find(e->pending.begin(), e->pending.end(), req_id));
+        e->reqs.erase(req_id);
+        return FPT_OK;
+    }
+    if (R->phase == kRunning) {
+        // lanes drop the request at the start of the next launch
+        R->phase = kCancelled;
+        static const int cancelled = kSlotCancelled;
+        cudaSetDevice(e->device);
+        const cudaError_t ce = cudaMemcpy(&e->d_ctl[R->slot].state, &cancelled, sizeof(int),
+                                          cudaMemcpyHostToDevice);
+        if (ce != cudaSuccess) {
+            e->broken = true;
+            return fail(e, FPT_ECUDA, std::string("cancel: ") + cudaGetErrorString(ce));
+        }
+        return FPT_OK;
+    }
+    if (R->slot < 0) {   // finished and its slot already recycled
+        free_request_buffers(*R, e);
+        e->reqs.erase(req_id);
+    }
+    return FPT_OK;
+}
+
+extern "C" fpt_status fpt_get_counters(fpt_engine *e, fpt_engine_counters *out) {
+    if (!e || !out) return fail(e, FPT_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(e->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->iterations = e->iterations;
+    out->useful_steps = e->h_counters[kCntUseful];
+    out->escapes = e->h_counters[kCntEscapes];
+    out->censored = e->h_counters[kCntCensored];
+    out->lane_step_slots = e->iterations * static_cast<uint64_t>(e->lanes) * e->chunk_blocks * 4;
+    out->lanes = e->lanes;
+    out->grid = e->grid;
+    out->block = e->block;
+    out->traj_per_thread = e->T;
+    out->chunk_steps = e->chunk_blocks * 4;
+    out->kernel_ms = e->kernel_ms;
+    for (int s = 0; s < e->maxr; ++s)
+        if (e->slot_req[s]) ++out->resident_requests;
+    out->pending_requests = static_cast<uint32_t>(e->pending.size());
+    return FPT_OK;
+}
+
+extern "C" void *fpt_engine_stream(fpt_engine *e) { return e ? static_cast<void *>(e->stream) : nullptr; }
+
+extern "C" fpt_status fpt_destroy(fpt_engine *e) {
+    if (!e) return fail(e, FPT_EINVAL, "NULL engine");
+    destroy_all(e);
+    delete e;
+    return FPT_OK;
+}
+
+extern "C" const char *fpt_last_error(fpt_engine *e) {
+    if (e) return t_engine_error.empty() ? e->error.c_str() : t_engine_error.c_str();
+    return get_error().c_str();
+}

@@ -1,0 +1,77 @@
+// engine_dev.h -- device data layout of the persistent batched engine (host + device).
+//
+// HBM layout (all allocated by the engine):
+//   SlotDev[max_requests]     read-only request constants (decoded on the host)
+//   SlotCtl[max_requests]     per-request work queue head, in-flight lane count, fair-share cap,
+//                             state and the running sums of the completed id-block prefix
+//   lane state, structure of arrays, one entry per lane (lanes = threads x T):
+//       r (wrapped phase), v, hb (upper event bound), w (winding), c (64-bit Philox block
+//       counter = completed 4-step blocks), gid (64-bit trajectory id), slot, budget
+//   per request: IdBlockAcc[n_idblocks] + u32 histogram rows [n_idblocks][hist_bins]
+//       (+ optional int64 escape step per trajectory)
+#pragma once
+
+#include <cstdint>
+
+namespace fpt {
+
+enum : int { kSlotFree = 0, kSlotActive = 1, kSlotFinished = 2, kSlotCancelled = 3 };
+
+// Exact accumulators of one block of stop_block consecutive trajectory ids.
+struct IdBlockAcc {
+    unsigned int done, escaped, under, over;
+    unsigned long long s1_lo, s1_hi;   // sum of escape steps (128-bit)
+    unsigned long long s2_lo, s2_hi;   // sum of squared escape steps (128-bit)
+};
+
+struct SlotDev {
+    // single-precision step constants
+    float dt, A, amp, bmc, nudt, v0, r0, eb0;
+    int32_t w0, model;
+    uint32_t key0, key1;
+    // trajectories and budget
+    uint64_t traj_offset, n_traj, max_steps, nblocks;   // nblocks = ceil(max_steps / 4)
+    double gamma0, nudt_d;                               // double bias ramp
+    // observable and histogram: x = out_a + out_b k
+    int32_t output, hist_bins;
+    double out_a, out_b, hist_lo, hist_hi, hist_inv_w;
+    // prefix stop rule
+    double stop_rse;
+    uint32_t stop_block, n_idblocks;
+    IdBlockAcc *acc;
+    unsigned int *hist;
+    long long *per_traj;
+};
+
+struct SlotCtl {
+    unsigned long long head;   // next trajectory index to hand out (may run past n_traj)
+    int inflight;              // lanes integrating a trajectory of this request
+    int state;                 // kSlot*
+    unsigned int prefix;       // id blocks folded into the running sums
+    unsigned int reserved;
+    unsigned long long n_done, n_esc, s1_lo, s1_hi, s2_lo, s2_hi, under, over;
+};
+
+struct LaneSoA {
+    float *r, *v, *hb;
+    int *w, *slot;
+    unsigned int *c_lo, *c_hi, *gid_lo, *gid_hi, *budget;
+};
+
+enum : int { kCntUseful = 0, kCntEscapes = 1, kCntCensored = 2, kCntCount = 4 };
+
+struct EngineDev {
+    SlotDev *slots;
+    SlotCtl *ctl;
+    const int *caps;        // [max_requests] fair-share lane caps
+    const int *act_list;    // [2][max_requests] claimable slots per model
+    const int *act_count;   // [2]
+    LaneSoA lanes;
+    int *warp_kind;         // model each warp currently integrates (-1 idle)
+    unsigned int *warp_cursor;
+    unsigned long long *counters;
+    unsigned int chunk_blocks;
+    int max_requests;
+};
+
+}  // namespace fpt

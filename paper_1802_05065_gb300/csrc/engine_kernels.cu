@@ -1,0 +1,460 @@
+// engine_kernels.cu -- the persistent batched FPT kernel and the completion scan.
+//
+// One launch ("chunk") advances every resident lane by up to chunk_blocks x 4 Euler-Maruyama
+// steps.  A lane integrates one trajectory: Philox4x32-10 -> Box-Muller -> step (Alg. 1 / 3)
+// on a phase wrapped to [-pi, pi) with an integer winding count.  Escape and wrap events are
+// caught by one compare per step (r >= hb || r < -pi); at the end of each 4-step block the warp
+// votes, finished lanes publish their exact result and the warp refills them from the
+// requests' work queues (warp-aggregated atomicAdd on the queue head), so lanes never wait for
+// the slowest trajectory of a batch (the dynamic job assignment of Sec. III.B, Fig. 6).
+//
+// A warp integrates one model at a time (underdamped or overdamped code path); the request of
+// each lane is free, so requests of the same model share warps.  Refill is round-robin over
+// the claimable requests with a fair-share cap on in-flight lanes per request (first pass),
+// then without cap (second pass), so no lane idles while any request has work.
+#include <cstdint>
+
+#include "engine_dev.h"
+#include "fpt_device.cuh"
+#include "internal.h"
+
+namespace fpt {
+
+namespace {
+
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+struct Lane {
+    float r, v, hb;
+    int w, slot, esc;
+    unsigned c_lo, c_hi, gid_lo, gid_hi, budget;
+    float dt, A, amp, bmc, nudt, gb;
+    unsigned k0, k1;
+};
+
+__device__ __forceinline__ float qnan_f() { return __int_as_float(0x7FFFFFFF); }
+
+template <typename V>
+__device__ __forceinline__ V vload(const V &x) {
+    return *const_cast<const volatile V *>(&x);
+}
+
+__device__ __forceinline__ void set_idle(Lane &L) {
+    L.slot = -1;
+    L.r = qnan_f();
+    L.v = 0.0f;
+    L.hb = 0.0f;
+    L.esc = -1;
+    L.budget = 0xFFFFFFFFu;
+    L.dt = L.A = L.amp = L.bmc = L.nudt = L.gb = 0.0f;
+    L.k0 = L.k1 = 0;
+}
+
+__device__ __forceinline__ unsigned clamp_u32(unsigned long long x) {
+    return x > 0xFFFFFFFFull ? 0xFFFFFFFFu : static_cast<unsigned>(x);
+}
+
+__device__ __forceinline__ void load_consts(Lane &L, const SlotDev *S) {
+    L.dt = S->dt;
+    L.A = S->A;
+    L.amp = S->amp;
+    L.bmc = S->bmc;
+    L.nudt = S->nudt;
+    L.k0 = S->key0;
+    L.k1 = S->key1;
+}
+
+// Start trajectory `idx` of request slot s at block b of this launch.  The single-precision
+// bias base gb is set so that gb + nudt * J equals gamma0 + nu dt k for this lane's step k,
+// with J = 4 b + (step within block) + 1 counted from the start of the launch.
+__device__ __forceinline__ void init_lane(Lane &L, const EngineDev &E, int s, unsigned long long idx, unsigned b) {
+    const SlotDev *S = E.slots + s;
+    const unsigned long long gid = S->traj_offset + idx;
+    L.slot = s;
+    L.gid_lo = static_cast<unsigned>(gid);
+    L.gid_hi = static_cast<unsigned>(gid >> 32);
+    L.c_lo = L.c_hi = 0;
+    L.r = S->r0;
+    L.v = S->v0;
+    L.w = S->w0;
+    L.hb = fminf(S->eb0, kPiF);
+    L.esc = -1;
+    L.budget = clamp_u32(S->nblocks);
+    load_consts(L, S);
+    L.gb = static_cast<float>(S->gamma0 - S->nudt_d * static_cast<double>(4ull * b));
+}
+
+__device__ __forceinline__ void atomic_add128(unsigned long long *lo_p, unsigned long long *hi_p,
+                                              unsigned long long alo, unsigned long long ahi) {
+    const unsigned long long old = atomicAdd(lo_p, alo);
+    const unsigned long long carry = (old + alo < old) ? 1ull : 0ull;
+    if (ahi + carry) atomicAdd(hi_p, ahi + carry);
+}
+
+// Publish one finished trajectory into its id block: exact sums of k and k^2, histogram bin of
+// x = out_a + out_b k (IEEE double, separately rounded), optional per-trajectory step, then the
+// completion count that the scan kernel reads.
+__device__ __forceinline__ void emit(const SlotDev *S, unsigned long long gid, bool escaped, unsigned long long k) {
+    const unsigned long long idx = gid - S->traj_offset;
+    const unsigned ib = static_cast<unsigned>(idx / S->stop_block);
+    IdBlockAcc *A = S->acc + ib;
+    if (escaped) {
+        atomicAdd(&A->escaped, 1u);
+        atomic_add128(&A->s1_lo, &A->s1_hi, k, 0ull);
+        atomic_add128(&A->s2_lo, &A->s2_hi, k * k, __umul64hi(k, k));
+        const double kd = static_cast<double>(k);
+        const double x = S->output == FPT_OUT_TIME ? __dmul_rn(S->out_b, kd)
+                                                   : __dadd_rn(S->out_a, __dmul_rn(S->out_b, kd));
+        if (x < S->hist_lo) {
+            atomicAdd(&A->under, 1u);
+        } else if (x >= S->hist_hi) {
+            atomicAdd(&A->over, 1u);
+        } else {
+            int bin = static_cast<int>(floor(__dmul_rn(__dsub_rn(x, S->hist_lo), S->hist_inv_w)));
+            if (bin >= S->hist_bins) bin = S->hist_bins - 1;
+            atomicAdd(S->hist + static_cast<size_t>(ib) * S->hist_bins + bin, 1u);
+        }
+    }
+    if (S->per_traj) S->per_traj[idx] = escaped ? static_cast<long long>(k) : -1ll;
+    atomicAdd(&A->done, 1u);
+}
+
+// Rare per-lane path: the phase left [-pi, min(eb, pi)).  eb = phi* - 2 pi w is the threshold
+// in the current cell's coordinates.  Escape freezes the lane (NaN phase: no further events)
+// and records the step within the block; otherwise wrap and count a winding.
+__device__ __forceinline__ void phase_event(Lane &L, const EngineDev &E, int s) {
+    const SlotDev *S = E.slots + L.slot;
+    const float eb0 = S->eb0;
+    const int w0 = S->w0;
+    const float eb = fmaf(-kTwoPiF, static_cast<float>(L.w - w0), eb0);
+    if (L.r >= eb) {
+        L.esc = s;
+        L.r = qnan_f();
+        return;
+    }
+    if (L.r >= kPiF) {
+        L.r -= kTwoPiF;
+        L.w += 1;
+    } else {
+        L.r += kTwoPiF;
+        L.w -= 1;
+    }
+    L.hb = fminf(fmaf(-kTwoPiF, static_cast<float>(L.w - w0), eb0), kPiF);
+}
+
+// Finish lanes that escaped in the last block or reached the step budget.
+template <int T>
+__device__ __forceinline__ void finish_lanes(Lane (&L)[T], const EngineDev &E, unsigned long long &useful,
+                             int &n_active, unsigned &n_esc, unsigned &n_cens) {
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        if (L[t].slot < 0) {
+            L[t].budget = 0xFFFFFFFFu;
+            continue;
+        }
+        const bool esc = L[t].esc >= 0;
+        if (!esc && L[t].budget != 0) continue;
+        const SlotDev *S = E.slots + L[t].slot;
+        const unsigned long long c = (static_cast<unsigned long long>(L[t].c_hi) << 32) | L[t].c_lo;
+        const unsigned long long max_steps = S->max_steps;
+        if (!esc) {
+            const unsigned long long nb = S->nblocks;
+            if (c < nb) {   // the 32-bit budget had saturated: re-arm
+                L[t].budget = clamp_u32(nb - c);
+                continue;
+            }
+        }
+        unsigned long long k = 0;
+        bool escaped = false;
+        if (esc) {
+            k = 4ull * (c - 1) + static_cast<unsigned long long>(L[t].esc) + 1ull;
+            escaped = k <= max_steps;
+        }
+        if (escaped) useful -= static_cast<unsigned long long>(3 - L[t].esc);
+        else useful -= 4ull * c - max_steps;
+        const unsigned long long gid = (static_cast<unsigned long long>(L[t].gid_hi) << 32) | L[t].gid_lo;
+        emit(S, gid, escaped, k);
+        if (escaped) ++n_esc;
+        else ++n_cens;
+        atomicSub(&E.ctl[L[t].slot].inflight, 1);
+        set_idle(L[t]);
+        --n_active;
+    }
+}
+
+// Warp-collective refill of idle lanes with trajectories of requests of model `kind`.
+template <int T>
+__device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, int kind, unsigned b, int &n_active,
+                       unsigned &cursor) {
+    const int lane = threadIdx.x & 31;
+    const unsigned lt = (1u << lane) - 1u;
+    unsigned idle[T];
+    int total = 0;
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        idle[t] = __ballot_sync(kFull, L[t].slot < 0);
+        total += __popc(idle[t]);
+    }
+    if (total == 0) return;
+    const int cnt = E.act_count[kind];
+    if (cnt <= 0) return;
+    const int *list = E.act_list + kind * E.max_requests;
+    for (int pass = 0; pass < 2 && total > 0; ++pass) {
+        for (int scanned = 0; scanned < cnt && total > 0; ++scanned) {
+            const int s = list[cursor % static_cast<unsigned>(cnt)];
+            ++cursor;
+            unsigned long long base = 0;
+            int got = 0;
+            if (lane == 0) {
+                SlotCtl *C = E.ctl + s;
+                if (vload(C->state) == kSlotActive) {
+                    int want = total;
+                    if (pass == 0) {
+                        const int room = E.caps[s] - vload(C->inflight);
+                        want = want < room ? want : room;
+                    }
+                    const unsigned long long n_traj = E.slots[s].n_traj;
+                    if (want > 0 && vload(C->head) < n_traj) {
+                        base = atomicAdd(&C->head, static_cast<unsigned long long>(want));
+                        if (base < n_traj) {
+                            const unsigned long long left = n_traj - base;
+                            got = left < static_cast<unsigned long long>(want) ? static_cast<int>(left) : want;
+                            atomicAdd(&C->inflight, got);
+                        }
+                    }
+                }
+            }
+            got = __shfl_sync(kFull, got, 0);
+            if (got == 0) continue;
+            base = __shfl_sync(kFull, base, 0);
+            int before = 0;
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                const unsigned m = idle[t];
+                const int rank = before + __popc(m & lt);
+                if (((m >> lane) & 1u) && rank < got) {
+                    init_lane(L[t], E, s, base + static_cast<unsigned long long>(rank), b);
+                    ++n_active;
+                }
+                before += __popc(m);
+                idle[t] = __ballot_sync(kFull, L[t].slot < 0);
+            }
+            total -= got;
+        }
+    }
+}
+
+// Integrate blocks of 4 steps with model M until the launch's block count is reached or the
+// whole warp has run out of work.  Returns the next block index.
+template <int M, int T>
+__device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E, unsigned b, int &n_active,
+                               unsigned &cursor, unsigned long long &useful, unsigned &n_esc,
+                               unsigned &n_cens) {
+    const unsigned nb = E.chunk_blocks;
+    while (b < nb) {
+        const float Jb = 4.0f * static_cast<float>(b);
+        float n[T][4];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            const uint4 x = philox4x32_10(make_uint4(L[t].c_lo, L[t].c_hi, L[t].gid_lo, L[t].gid_hi),
+                                          L[t].k0, L[t].k1);
+            bm_pair_f32(x.x, x.y, L[t].bmc, n[t][0], n[t][1]);
+            bm_pair_f32(x.z, x.w, L[t].bmc, n[t][2], n[t][3]);
+        }
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            const float J = Jb + static_cast<float>(s + 1);
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                step_f32<M>(L[t].r, L[t].v, n[t][s], fmaf(L[t].nudt, J, L[t].gb), L[t].dt, L[t].A,
+                            L[t].amp);
+                if (L[t].r >= L[t].hb || L[t].r < -kPiF) phase_event(L[t], E, s);
+            }
+        }
+        useful += 4ull * static_cast<unsigned>(n_active);
+        bool ev = false;
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            L[t].c_lo += 1u;
+            L[t].c_hi += (L[t].c_lo == 0u) ? 1u : 0u;
+            L[t].budget -= 1u;
+            ev |= (L[t].esc >= 0) || (L[t].budget == 0u);
+        }
+        ++b;
+        if (__any_sync(kFull, ev)) {
+            finish_lanes(L, E, useful, n_active, n_esc, n_cens);
+            refill(L, E, M, b, n_active, cursor);
+            if (!__any_sync(kFull, n_active > 0)) break;
+        }
+    }
+    return b;
+}
+
+template <int T>
+__global__ void __launch_bounds__(256) engine_chunk_kernel(EngineDev E) {
+    const unsigned nthreads = gridDim.x * blockDim.x;
+    const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
+    const unsigned warp = gtid >> 5;
+    const int lane = threadIdx.x & 31;
+    Lane L[T];
+    int n_active = 0;
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const unsigned i = t * nthreads + gtid;
+        int s = E.lanes.slot[i];
+        if (s >= 0 && vload(E.ctl[s].state) != kSlotActive) {   // request finished or cancelled
+            atomicSub(&E.ctl[s].inflight, 1);
+            s = -1;
+        }
+        if (s < 0) {
+            set_idle(L[t]);
+            continue;
+        }
+        const SlotDev *S = E.slots + s;
+        L[t].slot = s;
+        L[t].r = E.lanes.r[i];
+        L[t].v = E.lanes.v[i];
+        L[t].hb = E.lanes.hb[i];
+        L[t].w = E.lanes.w[i];
+        L[t].c_lo = E.lanes.c_lo[i];
+        L[t].c_hi = E.lanes.c_hi[i];
+        L[t].gid_lo = E.lanes.gid_lo[i];
+        L[t].gid_hi = E.lanes.gid_hi[i];
+        L[t].budget = E.lanes.budget[i];
+        L[t].esc = -1;
+        load_consts(L[t], S);
+        const unsigned long long c = (static_cast<unsigned long long>(L[t].c_hi) << 32) | L[t].c_lo;
+        L[t].gb = static_cast<float>(S->gamma0 + S->nudt_d * static_cast<double>(4ull * c));
+        ++n_active;
+    }
+    int kind = E.warp_kind[warp];
+    if (!__any_sync(kFull, n_active > 0)) kind = -1;
+    unsigned cursor = E.warp_cursor[warp];
+    unsigned long long useful = 0;
+    unsigned n_esc = 0, n_cens = 0;
+    if (kind >= 0) refill(L, E, kind, 0u, n_active, cursor);
+    unsigned b = 0;
+    while (b < E.chunk_blocks) {
+        if (kind < 0) {
+            const int first = static_cast<int>(warp & 1u);
+            for (int q = 0; q < 2 && kind < 0; ++q) {
+                const int m = first ^ q;
+                refill(L, E, m, b, n_active, cursor);
+                if (__any_sync(kFull, n_active > 0)) kind = m;
+            }
+            if (kind < 0) break;
+        }
+        if (kind == kUnder)
+            b = run_blocks<kUnder, T>(L, E, b, n_active, cursor, useful, n_esc, n_cens);
+        else
+            b = run_blocks<kOver, T>(L, E, b, n_active, cursor, useful, n_esc, n_cens);
+        if (!__any_sync(kFull, n_active > 0)) kind = -1;
+    }
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const unsigned i = t * nthreads + gtid;
+        E.lanes.slot[i] = L[t].slot;
+        if (L[t].slot < 0) continue;
+        E.lanes.r[i] = L[t].r;
+        E.lanes.v[i] = L[t].v;
+        E.lanes.hb[i] = L[t].hb;
+        E.lanes.w[i] = L[t].w;
+        E.lanes.c_lo[i] = L[t].c_lo;
+        E.lanes.c_hi[i] = L[t].c_hi;
+        E.lanes.gid_lo[i] = L[t].gid_lo;
+        E.lanes.gid_hi[i] = L[t].gid_hi;
+        E.lanes.budget[i] = L[t].budget;
+    }
+    if (lane == 0) {
+        E.warp_kind[warp] = kind;
+        E.warp_cursor[warp] = cursor;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        useful += __shfl_down_sync(kFull, useful, off);
+        n_esc += __shfl_down_sync(kFull, n_esc, off);
+        n_cens += __shfl_down_sync(kFull, n_cens, off);
+    }
+    if (lane == 0) {
+        if (useful) atomicAdd(&E.counters[kCntUseful], useful);
+        if (n_esc) atomicAdd(&E.counters[kCntEscapes], static_cast<unsigned long long>(n_esc));
+        if (n_cens) atomicAdd(&E.counters[kCntCensored], static_cast<unsigned long long>(n_cens));
+    }
+}
+
+__device__ __forceinline__ double u128_to_d(unsigned long long lo, unsigned long long hi) {
+    return __dadd_rn(__dmul_rn(static_cast<double>(hi), 18446744073709551616.0),
+                     static_cast<double>(lo));
+}
+
+// Fold completed id blocks, in id order, into each request's running sums; stop at the first
+// prefix meeting the relative-standard-error rule, or when every block is complete.
+__global__ void engine_scan_kernel(EngineDev E) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= E.max_requests) return;
+    SlotCtl *C = E.ctl + s;
+    if (C->state != kSlotActive) return;
+    const SlotDev *S = E.slots + s;
+    unsigned p = C->prefix;
+    bool finished = false;
+    while (p < S->n_idblocks) {
+        const unsigned long long first = static_cast<unsigned long long>(p) * S->stop_block;
+        const unsigned long long left = S->n_traj - first;
+        const unsigned need = left < S->stop_block ? static_cast<unsigned>(left) : S->stop_block;
+        const IdBlockAcc &A = S->acc[p];
+        if (A.done < need) break;
+        C->n_done += A.done;
+        C->n_esc += A.escaped;
+        C->under += A.under;
+        C->over += A.over;
+        C->s1_lo += A.s1_lo;
+        C->s1_hi += A.s1_hi + (C->s1_lo < A.s1_lo ? 1ull : 0ull);
+        C->s2_lo += A.s2_lo;
+        C->s2_hi += A.s2_hi + (C->s2_lo < A.s2_lo ? 1ull : 0ull);
+        ++p;
+        if (S->stop_rse > 0.0 && C->n_esc >= 2) {
+            const double n = static_cast<double>(C->n_esc);
+            const double s1 = u128_to_d(C->s1_lo, C->s1_hi);
+            const double s2 = u128_to_d(C->s2_lo, C->s2_hi);
+            const double mk = __ddiv_rn(s1, n);
+            double vk = __ddiv_rn(__dsub_rn(s2, __dmul_rn(s1, mk)), __dsub_rn(n, 1.0));
+            if (vk < 0.0) vk = 0.0;
+            const double mx = S->output == FPT_OUT_TIME ? __dmul_rn(S->out_b, mk)
+                                                        : __dadd_rn(S->out_a, __dmul_rn(S->out_b, mk));
+            const double se = __dmul_rn(fabs(S->out_b), __dsqrt_rn(__ddiv_rn(vk, n)));
+            if (se <= __dmul_rn(S->stop_rse, fabs(mx))) {
+                finished = true;
+                break;
+            }
+        }
+    }
+    C->prefix = p;
+    if (p >= S->n_idblocks) finished = true;
+    if (finished) C->state = kSlotFinished;
+}
+
+}  // namespace
+
+cudaError_t launch_engine_chunk(const EngineDev &E, int T, unsigned grid, unsigned block,
+                                cudaStream_t s) {
+    if (T == 1) engine_chunk_kernel<1><<<grid, block, 0, s>>>(E);
+    else engine_chunk_kernel<2><<<grid, block, 0, s>>>(E);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_engine_scan(const EngineDev &E, cudaStream_t s) {
+    const unsigned block = 128;
+    const unsigned grid = (static_cast<unsigned>(E.max_requests) + block - 1) / block;
+    engine_scan_kernel<<<grid, block, 0, s>>>(E);
+    return cudaGetLastError();
+}
+
+cudaError_t engine_chunk_occupancy(int T, int block, int *blocks_per_sm) {
+    if (T == 1)
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, engine_chunk_kernel<1>,
+                                                             block, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, engine_chunk_kernel<2>,
+                                                         block, 0);
+}
+
+}  // namespace fpt

@@ -1,0 +1,108 @@
+// fpt_device.cuh -- device primitives of the FPT hot path (sm_103a).
+//
+//   philox4x32_10   counter-based generator (Salmon et al., SC'11), all in registers
+//   bm_pair_f32     Box-Muller (Sec. III.B, nrand) in single precision, noise-scaled
+//   bm_pair_f64     Box-Muller in double precision, same arithmetic order as the FP64 oracle
+//   step_f32<M>     one Euler-Maruyama step of Alg. 1 / Alg. 3 on a wrapped phase
+//
+// Keying (fixed once for the whole library): key = (seed lo, seed hi), counter =
+// (block lo, block hi, trajectory lo, trajectory hi); block b feeds steps 4b+1 .. 4b+4, words
+// (x0,x1) -> normals of steps 4b+1, 4b+2 and (x2,x3) -> steps 4b+3, 4b+4.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace fpt {
+
+constexpr uint32_t kPhiloxM0 = 0xD2511F53u;
+constexpr uint32_t kPhiloxM1 = 0xCD9E8D57u;
+constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
+constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
+
+constexpr float kPiF = 3.14159265358979323846f;
+constexpr float kTwoPiF = 6.28318530717958647692f;
+
+// Philox4x32-10: ten rounds of two 32x32->64 multiplies; the key advances by the Weyl
+// constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint64_t p0 = static_cast<uint64_t>(kPhiloxM0) * c.x;
+        const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * c.z;
+        const uint32_t hi0 = static_cast<uint32_t>(p0 >> 32), lo0 = static_cast<uint32_t>(p0);
+        const uint32_t hi1 = static_cast<uint32_t>(p1 >> 32), lo1 = static_cast<uint32_t>(p1);
+        c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+        k0 += kPhiloxW0;
+        k1 += kPhiloxW1;
+    }
+    return c;
+}
+
+// Single-precision uniform in (0, 1) from the low 23 bits of a word: u = (m + 1/2) 2^-23.
+// (1 + m 2^-23) - (1 - 2^-24) is exact (Sterbenz), so no int->float conversion is needed.
+__device__ __forceinline__ float uniform_f32(uint32_t x) {
+    return __uint_as_float((x & 0x007FFFFFu) | 0x3F800000u) - 0.99999994039535522f;
+}
+
+// Box-Muller pair scaled by the step noise: with bmc = -2 ln(2) sigma^2,
+// sigma*R = sqrt(bmc * log2(u1)), theta = 2 pi u2, n0 = sigma R cos theta, n1 = sigma R sin theta.
+// The radicand is clamped at 0: the fast log2 can return a tiny positive value for u1 near 1.
+__device__ __forceinline__ void bm_pair_f32(uint32_t x0, uint32_t x1, float bmc, float &n0,
+                                            float &n1) {
+    const float u1 = uniform_f32(x0);
+    const float u2 = uniform_f32(x1);
+    const float rr = sqrtf(fmaxf(bmc * __log2f(u1), 0.0f));
+    float sn, cs;
+    __sincosf(kTwoPiF * u2, &sn, &cs);
+    n0 = rr * cs;
+    n1 = rr * sn;
+}
+
+// Double-precision uniform in (0, 1): u = (x + 1/2) 2^-32, exact.
+__device__ __forceinline__ double uniform_f64(uint32_t x) {
+    return __dmul_rn(__dadd_rn(static_cast<double>(x), 0.5), 2.3283064365386962890625e-10);
+}
+
+// Box-Muller in double precision, evaluated in the order R = sqrt(-2 log u1), theta = (2 pi) u2,
+// z0 = R cos theta, z1 = R sin theta, each operation rounded separately.
+__device__ __forceinline__ void bm_pair_f64(uint32_t x0, uint32_t x1, double &z0, double &z1) {
+    const double u1 = uniform_f64(x0);
+    const double u2 = uniform_f64(x1);
+    const double r = __dsqrt_rn(__dmul_rn(-2.0, log(u1)));
+    const double theta = __dmul_rn(6.283185307179586476925286766559, u2);
+    z0 = __dmul_rn(r, cos(theta));
+    z1 = __dmul_rn(r, sin(theta));
+}
+
+// Per-lane constants of the FP32 step, decoded from a request on the host (Alg. 1 lines 4-7).
+struct StepConstF32 {
+    float dt;     // h
+    float A;      // 1 - alpha dt (underdamped velocity decay)
+    float amp;    // amplitude of the sin term
+    float bmc;    // -2 ln 2 sigma^2 (Box-Muller radius in log2 form)
+    float nudt;   // bias increment per step (Alg. 3: delta-gamma)
+};
+
+enum : int { kUnder = 0, kOver = 1 };
+
+// One Euler-Maruyama step with noise increment n = sigma z and bias g = gamma_k:
+//   underdamped: phi += v dt;  v = (1 - alpha dt) v + (g - A sin phi_old) dt + n
+//   overdamped : phi += (g - A sin phi_old) dt + n
+// Both updates read the state of the previous step (Alg. 1 lines 11-12).  r is the phase
+// wrapped to [-pi, pi); the caller restores the range and counts windings.
+template <int M>
+__device__ __forceinline__ void step_f32(float &r, float &v, float n, float g, float dt, float A,
+                                         float amp) {
+    const float s = __sinf(r);
+    const float f = fmaf(-amp, s, g);
+    if constexpr (M == kUnder) {
+        const float vn = fmaf(A, v, fmaf(dt, f, n));
+        r = fmaf(dt, v, r);
+        v = vn;
+    } else {
+        r = fmaf(dt, f, r) + n;
+    }
+}
+
+}  // namespace fpt

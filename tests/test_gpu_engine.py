@@ -1,0 +1,200 @@
+"""Persistent batched engine (GPU): parity with the one-trajectory-per-thread FP32 kernel and the
+oracle, determinism under batching, the prefix stop rule, censoring and error paths."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from oracle import mfpt, stats
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    import paper_1802_05065_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1802_05065_gb300 import api as _api
+    return _api
+
+
+def _engine(lib, **kw):
+    kw.setdefault("chunk_steps", 4096)
+    return lib.Engine(0, **kw)
+
+
+def _run(eng, d, n, seed, **over):
+    rid = eng.submit(lib_params(d, **over), n, seed)
+    res = eng.wait(rid, 600.0)
+    return rid, res
+
+
+def lib_params(d, **over):
+    import paper_1802_05065_gb300 as m
+    return m.params_from(d, **over)
+
+
+CONST_OVER = workloads.scaled(workloads.overdamped_sweep(n_traj=1)[11], max_steps=10**8)
+CONST_UNDER = workloads.scaled(workloads.plain_constant_tilt(), D=0.05, precision="fp32",
+                               max_steps=10**6, hist_hi=2000.0)
+
+
+@pytest.mark.parametrize("d", [CONST_OVER, CONST_UNDER], ids=["overdamped", "underdamped"])
+@pytest.mark.parametrize("T", [1, 2])
+def test_engine_matches_plain_fp32_per_trajectory(lib, api, d, T):
+    """Constant bias: the engine's lanes run the same single-precision arithmetic as the plain
+    kernel, so every trajectory's escape step is identical, whatever lane ran it."""
+    n, seed = 5000, 31
+    with _engine(lib, traj_per_thread=T) as eng:
+        rid, res = _run(eng, d, n, seed, keep_per_traj=1)
+        e_steps = eng.per_traj_steps(rid, n)
+    p_steps = api.run_plain(d, n, seed).cpu().numpy()
+    assert (e_steps == p_steps).all()
+    s = stats.summarize(oracle.params_from(d), e_steps)
+    assert res.n_used == n and res.n_escaped == s.n_escaped
+    assert math.isclose(res.mean, s.mean, rel_tol=1e-12)
+    assert math.isclose(res.var, s.var, rel_tol=1e-9)
+
+
+def test_engine_histogram_and_sums_exact(lib):
+    d = workloads.scaled(CONST_UNDER, hist_bins=64, hist_lo=0.0, hist_hi=800.0)
+    with _engine(lib) as eng:
+        rid, res = _run(eng, d, 3000, 8, keep_per_traj=1)
+        steps = eng.per_traj_steps(rid, 3000)
+        h, u, o = eng.histogram(rid, 64)
+    s = stats.summarize(oracle.params_from(d), steps)
+    assert list(h) == list(s.hist) and u == s.under and o == s.over
+    assert res.steps_total == sum(int(k) if k >= 0 else d["max_steps"] for k in steps)
+
+
+def test_engine_statistics_vs_oracle(lib):
+    """Underdamped constant tilt, FP32 engine vs FP64 oracle with independent seeds."""
+    d = CONST_UNDER
+    with _engine(lib) as eng:
+        rid, res = _run(eng, d, 2**15, 101, keep_per_traj=1)
+        g = eng.per_traj_steps(rid, 2**15)
+    r = oracle.run(oracle.params_from(d), 202, 3000)
+    p = oracle.params_from(d)
+    sr = stats.summarize(p, r)
+    assert stats.within_combined_se(res.mean, res.sem, sr.mean, sr.sem, 3.0)
+    assert stats.ks_pvalue(stats.observables(p, g), stats.observables(p, r)) > 0.01
+
+
+def test_engine_ramp_vs_oracle(lib):
+    """Alg. 3 (switching bias) with a fast ramp: FP32 engine vs FP64 oracle."""
+    d = workloads.ramp_sweep(n_traj=1, rates=(1e-4,))[0]
+    with _engine(lib) as eng:
+        rid, res = _run(eng, d, 2**14, 5, keep_per_traj=1)
+        g = eng.per_traj_steps(rid, 2**14)
+    r = oracle.run(oracle.params_from(d), 6, 1500)
+    p = oracle.params_from(d)
+    sr = stats.summarize(p, r)
+    assert res.n_censored == 0 and sr.n_censored == 0
+    assert stats.within_combined_se(res.mean, res.sem, sr.mean, sr.sem, 3.0)
+    assert stats.ks_pvalue(stats.observables(p, g), stats.observables(p, r)) > 0.01
+
+
+def test_batch_invariance(lib):
+    """A request gives the same per-trajectory steps, histogram and sums alone and inside an
+    uneven batch of requests of both models."""
+    target = workloads.scaled(CONST_UNDER, hist_bins=50, hist_hi=1000.0)
+    n, seed = 6000, 17
+    with _engine(lib) as eng:
+        rid, alone = _run(eng, target, n, seed, keep_per_traj=1)
+        s_alone = eng.per_traj_steps(rid, n)
+        h_alone = eng.histogram(rid, 50)
+    mix = [(CONST_OVER, 20000, 1), (workloads.scaled(CONST_UNDER, D=0.08), 9000, 2),
+           (workloads.ramp_sweep(n_traj=1, rates=(1e-3,))[0], 7000, 3)]
+    with _engine(lib, chunk_steps=1024) as eng:
+        others = [eng.submit(lib_params(d), k, s) for d, k, s in mix[:2]]
+        rid = eng.submit(lib_params(target, keep_per_traj=1), n, seed)
+        others.append(eng.submit(lib_params(mix[2][0]), mix[2][1], mix[2][2]))
+        mixed = eng.wait(rid, 600.0)
+        s_mix = eng.per_traj_steps(rid, n)
+        h_mix = eng.histogram(rid, 50)
+        for o in others:
+            eng.wait(o, 600.0)
+    assert (s_alone == s_mix).all()
+    assert h_alone == h_mix
+    assert (alone.mean, alone.var, alone.n_escaped) == (mixed.mean, mixed.var, mixed.n_escaped)
+
+
+def test_stop_rule_prefix_matches_oracle_rule(lib):
+    """The engine stops at the first whole-block prefix with relative SE <= target; the
+    oracle's rule applied to the same escape steps keeps the same prefix."""
+    d = workloads.scaled(CONST_OVER, stop_rse=0.02, stop_block=256)
+    n = 2**16
+    with _engine(lib) as eng:
+        rid, res = _run(eng, d, n, 41, keep_per_traj=1)
+        steps = eng.per_traj_steps(rid, n)
+    assert res.n_used < n
+    used = steps[: res.n_used]
+    assert (used != -2).all()
+    want = stats.stop_prefix(oracle.params_from(d), used, 0.02, 256)
+    assert res.n_used == want
+    s = stats.summarize(oracle.params_from(d), used)
+    assert math.isclose(res.mean, s.mean, rel_tol=1e-12)
+    assert res.sem <= 0.02 * res.mean
+
+
+def test_censoring_and_budget(lib):
+    """A tiny step budget censors every trajectory; a budget not a multiple of 4 censors at
+    exactly max_steps (escape after the budget counts as censored)."""
+    d = workloads.scaled(CONST_UNDER, max_steps=1001)
+    with _engine(lib) as eng:
+        rid, res = _run(eng, d, 4000, 3, keep_per_traj=1)
+        steps = eng.per_traj_steps(rid, 4000)
+    assert res.n_censored + res.n_escaped == 4000
+    assert (steps[steps >= 0] <= 1001).all()
+    d0 = workloads.scaled(CONST_UNDER, D=0.0)
+    with _engine(lib) as eng:
+        rid, res = _run(eng, workloads.scaled(d0, max_steps=5000), 700, 3)
+    assert res.n_censored == 700 and math.isnan(res.mean)
+
+
+def test_ragged_and_tiny_requests(lib, api):
+    with _engine(lib) as eng:
+        for n in (1, 31, 33, 4097):
+            rid, res = _run(eng, CONST_OVER, n, 5, keep_per_traj=1)
+            steps = eng.per_traj_steps(rid, n)
+            assert res.n_used == n
+            ref = api.run_plain(CONST_OVER, n, 5).cpu().numpy()
+            assert (steps == ref).all()
+
+
+def test_full_size_overdamped_point_vs_quadrature(lib):
+    """gamma = 0.9, D = 0.2 at the full 2^20 trajectories: mean escape time vs the exact
+    MFPT quadrature (3 SE plus 1 % for the Euler and discrete-monitoring bias at dt = 1e-3)."""
+    d = workloads.overdamped_sweep()[11]
+    with _engine(lib, chunk_steps=16384) as eng:
+        rid, res = _run(eng, d, d["n_traj"], d["seed"])
+    T = mfpt.overdamped_mfpt(0.9, 0.2)
+    assert res.n_used == 2**20 and res.n_censored == 0
+    assert stats.within_combined_se(res.mean, res.sem, T, 0.0, 3.0, allowance=0.01 * T)
+
+
+def test_errors(lib):
+    with _engine(lib) as eng:
+        with pytest.raises(lib.FptError) as ei:
+            eng.poll(999)
+        assert ei.value.status == -4
+        with pytest.raises(lib.FptError):
+            eng.submit(lib_params(CONST_OVER, precision="fp64"), 10, 1)
+        with pytest.raises(lib.FptError):
+            eng.submit(lib_params(CONST_OVER), 0, 1)
+        with pytest.raises(lib.FptError):
+            eng.submit(lib_params(CONST_OVER, hist_bins=0), 10, 1)
+        rid = eng.submit(lib_params(CONST_OVER, max_steps=2**40), 100000, 1)
+        eng.step(2)
+        eng.release(rid)          # cancel while running
+        eng.step(2)
+        with pytest.raises(lib.FptError):
+            eng.poll(rid)
+        c = eng.counters()
+        assert c["resident_requests"] == 0

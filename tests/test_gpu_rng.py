@@ -1,0 +1,58 @@
+"""Device random numbers vs. the oracle and vs. cuRAND (GPU)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def api():
+    from paper_1802_05065_gb300 import api as _api
+    return _api
+
+
+@pytest.mark.parametrize("seed,traj,block0", [(1, 0, 0), (0xDEADBEEFCAFEF00D, 2**32 + 5, 2**32 - 3),
+                                              (12345, 777, 10**9)])
+def test_philox_bit_exact_vs_oracle(api, seed, traj, block0):
+    n = 4096
+    dev = api.philox_words(seed, traj, block0, n)
+    for j in range(0, n, 97):
+        want = oracle.philox_block(seed, traj, block0 + j)
+        assert (dev[j] == want).all(), (j, dev[j], want)
+
+
+def test_philox_matches_curand(api):
+    """Block b of trajectory t equals cuRAND Philox4_32_10 words 4b..4b+3 of (seed, subsequence t)."""
+    seed, traj0, nseq, nwords, offset = 0x0123456789ABCDEF, 1000, 64, 64, 4 * 12345
+    cur = api.curand_philox_words(seed, traj0, offset, nseq, nwords)
+    for j in range(nseq):
+        mine = api.philox_words(seed, traj0 + j, offset // 4, nwords // 4).reshape(-1)
+        assert (mine == cur[j]).all(), j
+
+
+def test_fp64_normals_match_oracle(api):
+    """FP64 Box-Muller on the device vs the oracle's: identical except for rare last-ulp
+    differences of the device's log / sin / cos."""
+    seed, traj = 99, 3
+    dev = api.normals(1, seed, traj, 0, 4000)
+    ref = oracle.normals(seed, traj, 4000)
+    rel = np.abs(dev - ref) / np.maximum(np.abs(ref), 1e-300)
+    assert np.max(rel) < 1e-13
+    assert np.mean(dev == ref) > 0.9
+
+
+def test_fp32_normals_law(api):
+    """FP32 map (23-bit uniforms, fast log2 / sincos): unit normal law and close to the FP64
+    normals of the same words."""
+    from scipy import stats
+    z = np.concatenate([api.normals(0, 7, t, 0, 20000) for t in range(10)])
+    n = z.size
+    assert abs(z.mean()) < 5 / math.sqrt(n)
+    assert abs(z.var() - 1) < 5 * math.sqrt(2 / n)
+    assert stats.kstest(z, "norm").pvalue > 1e-3
+    z64 = api.normals(1, 7, 0, 0, 20000)
+    assert np.max(np.abs(z[:20000] - z64)) < 2e-3
