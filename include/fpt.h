@@ -180,6 +180,10 @@ fpt_status fpt_wait(fpt_engine *e, uint64_t req_id, double timeout_s, fpt_result
 fpt_status fpt_histogram(fpt_engine *e, uint64_t req_id, uint64_t *counts, int nbins,
                          uint64_t *under, uint64_t *over);
 
+/* Exact sums (host fpt_sums) over the used prefix of a finished request, for merging results
+ * of requests sharded across GPUs (integer addition of the fields is exact). */
+fpt_status fpt_request_sums(fpt_engine *e, uint64_t req_id, fpt_sums *out);
+
 /* Per-trajectory x (host, n doubles; -1 for censored when output = time, NaN for bias), for
  * requests submitted with keep_per_traj = 1.  Entries past n_used are not part of the result. */
 fpt_status fpt_per_traj(fpt_engine *e, uint64_t req_id, double *out, uint64_t n);

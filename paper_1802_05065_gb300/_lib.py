@@ -88,6 +88,7 @@ EXPORTS = [
     "fpt_step", "fpt_poll", "fpt_wait", "fpt_histogram", "fpt_per_traj", "fpt_per_traj_steps",
     "fpt_release", "fpt_get_counters", "fpt_engine_stream", "fpt_destroy", "fpt_last_error",
     "fpt_status_string", "fpt_philox_fill", "fpt_normals_fill", "fpt_version",
+    "fpt_request_sums",
 ]
 
 _lib = None
@@ -114,6 +115,7 @@ def load() -> ctypes.CDLL:
     L.fpt_wait.argtypes = [vp, u64, f64, P(Result)]
     L.fpt_histogram.argtypes = [vp, u64, P(u64), i32, P(u64), P(u64)]
     L.fpt_per_traj.argtypes = [vp, u64, P(f64), u64]
+    L.fpt_request_sums.argtypes = [vp, u64, P(Sums)]
     L.fpt_per_traj_steps.argtypes = [vp, u64, P(ctypes.c_int64), u64]
     L.fpt_release.argtypes = [vp, u64]
     L.fpt_get_counters.argtypes = [vp, P(EngineCounters)]
@@ -130,7 +132,7 @@ def load() -> ctypes.CDLL:
     for name in ("fpt_plain_launch", "fpt_reduce_steps", "fpt_sums_finish", "fpt_create",
                  "fpt_submit", "fpt_step", "fpt_poll", "fpt_wait", "fpt_histogram",
                  "fpt_per_traj", "fpt_per_traj_steps", "fpt_release", "fpt_get_counters",
-                 "fpt_destroy", "fpt_philox_fill", "fpt_normals_fill"):
+                 "fpt_destroy", "fpt_philox_fill", "fpt_normals_fill", "fpt_request_sums"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -264,6 +266,11 @@ class Engine:
         _check(self._L.fpt_per_traj(
             self._h, rid, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), n), self._h)
         return out
+
+    def exact_sums(self, rid: int) -> Sums:
+        s = Sums()
+        _check(self._L.fpt_request_sums(self._h, rid, ctypes.byref(s)), self._h)
+        return s
 
     def release(self, rid: int):
         _check(self._L.fpt_release(self._h, rid), self._h)

@@ -1,4 +1,4 @@
-// common.cpp -- request decoding (Alg. 1 lines 4-7, Alg. 3 lines 5-9), exact-sum results and
+// common.cpp -- request decoding (the set-up of Alg. 1 and Alg. 3), exact-sum results and
 // error strings.  Host code; built with floating-point contraction off so every double
 // expression rounds as written.
 #include <cfloat>

@@ -2,7 +2,7 @@
 //
 // One engine iteration:
 //   1. admission: queued requests take a free slot when their device memory fits the budget;
-//      their decoded constants (Alg. 1 lines 4-7, Alg. 3 lines 5-9) are copied into the slot
+//      their decoded constants (the set-up of Alg. 1 / Alg. 3) are copied into the slot
 //      table and their accumulators are zeroed;
 //   2. the claimable-slot lists and fair-share caps are refreshed (pinned host -> device);
 //   3. one resident-kernel launch advances every lane by up to chunk_steps steps;
@@ -469,7 +469,12 @@ fpt_status create_impl(const fpt_engine_config *cfg_in, fpt_engine *e) {
     ls.budget = reinterpret_cast<unsigned *>(m + 9 * L * 4);
     CK(cudaMemsetAsync(ls.slot, 0xFF, L * 4, e->stream));
     CK(cudaMemsetAsync(e->d_warp_kind, 0xFF, nwarps * sizeof(int), e->stream));
-    CK(cudaMemsetAsync(e->d_warp_cursor, 0, nwarps * sizeof(unsigned), e->stream));
+    {   // stagger the warps' round-robin cursors so the first claims spread over all requests
+        std::vector<unsigned> cur(nwarps);
+        for (unsigned w = 0; w < nwarps; ++w) cur[w] = w;
+        CK(cudaMemcpy(e->d_warp_cursor, cur.data(), nwarps * sizeof(unsigned),
+                      cudaMemcpyHostToDevice));
+    }
     CK(cudaMemsetAsync(e->d_counters, 0, kCntCount * sizeof(unsigned long long), e->stream));
     CK(cudaMallocHost(&e->h_slots, R * sizeof(SlotDev)));
     CK(cudaMallocHost(&e->h_ctl, R * sizeof(SlotCtl)));
@@ -646,6 +651,16 @@ extern "C" fpt_status fpt_histogram(fpt_engine *e, uint64_t req_id, uint64_t *co
     std::fill(counts, counts + nbins, 0ull);
     for (unsigned p = 0; p < prefix; ++p)
         for (int b = 0; b < nbins; ++b) counts[b] += rows[static_cast<size_t>(p) * nbins + b];
+    return FPT_OK;
+}
+
+extern "C" fpt_status fpt_request_sums(fpt_engine *e, uint64_t req_id, fpt_sums *out) {
+    if (!e || !out) return fail(e, FPT_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lk(e->mu);
+    Request *R = find(e, req_id);
+    if (!R) return fail(e, FPT_ENOTFOUND, "unknown request id");
+    if (R->phase != kFinished) return fail(e, FPT_PENDING, "request not finished");
+    *out = R->sums;
     return FPT_OK;
 }
 

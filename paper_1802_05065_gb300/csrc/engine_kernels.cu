@@ -206,21 +206,26 @@ __device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, int kin
             unsigned long long base = 0;
             int got = 0;
             if (lane == 0) {
+                // Reserve in-flight places first (exact fair-share cap in the first pass), then
+                // claim ids from the queue head; unused reservations are given back.
                 SlotCtl *C = E.ctl + s;
-                if (vload(C->state) == kSlotActive) {
+                const unsigned long long n_traj = E.slots[s].n_traj;
+                if (vload(C->state) == kSlotActive && vload(C->head) < n_traj) {
                     int want = total;
+                    const int prev = atomicAdd(&C->inflight, want);
                     if (pass == 0) {
-                        const int room = E.caps[s] - vload(C->inflight);
-                        want = want < room ? want : room;
+                        const int room = E.caps[s] - prev;
+                        const int allowed = room < 0 ? 0 : (room < want ? room : want);
+                        if (allowed < want) atomicSub(&C->inflight, want - allowed);
+                        want = allowed;
                     }
-                    const unsigned long long n_traj = E.slots[s].n_traj;
-                    if (want > 0 && vload(C->head) < n_traj) {
+                    if (want > 0) {
                         base = atomicAdd(&C->head, static_cast<unsigned long long>(want));
                         if (base < n_traj) {
                             const unsigned long long left = n_traj - base;
                             got = left < static_cast<unsigned long long>(want) ? static_cast<int>(left) : want;
-                            atomicAdd(&C->inflight, got);
                         }
+                        if (got < want) atomicSub(&C->inflight, want - got);
                     }
                 }
             }

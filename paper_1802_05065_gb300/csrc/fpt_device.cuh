@@ -39,10 +39,12 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
-// Single-precision uniform in (0, 1) from the low 23 bits of a word: u = (m + 1/2) 2^-23.
-// (1 + m 2^-23) - (1 - 2^-24) is exact (Sterbenz), so no int->float conversion is needed.
+// Single-precision uniform in (0, 1) from the high 23 bits m = x >> 9 of a word:
+// u = (m + 1/2) 2^-23, the double-precision uniform (x + 1/2) 2^-32 rounded to 23 bits, so the
+// FP32 and FP64 normals of one trajectory stay close.  (1 + m 2^-23) - (1 - 2^-24) is exact
+// (Sterbenz), so no int->float conversion is needed.
 __device__ __forceinline__ float uniform_f32(uint32_t x) {
-    return __uint_as_float((x & 0x007FFFFFu) | 0x3F800000u) - 0.99999994039535522f;
+    return __uint_as_float((x >> 9) | 0x3F800000u) - 0.99999994039535522f;
 }
 
 // Box-Muller pair scaled by the step noise: with bmc = -2 ln(2) sigma^2,
@@ -75,7 +77,7 @@ __device__ __forceinline__ void bm_pair_f64(uint32_t x0, uint32_t x1, double &z0
     z1 = __dmul_rn(r, sin(theta));
 }
 
-// Per-lane constants of the FP32 step, decoded from a request on the host (Alg. 1 lines 4-7).
+// Per-lane constants of the FP32 step, decoded from a request on the host (set-up of Alg. 1).
 struct StepConstF32 {
     float dt;     // h
     float A;      // 1 - alpha dt (underdamped velocity decay)
@@ -89,7 +91,7 @@ enum : int { kUnder = 0, kOver = 1 };
 // One Euler-Maruyama step with noise increment n = sigma z and bias g = gamma_k:
 //   underdamped: phi += v dt;  v = (1 - alpha dt) v + (g - A sin phi_old) dt + n
 //   overdamped : phi += (g - A sin phi_old) dt + n
-// Both updates read the state of the previous step (Alg. 1 lines 11-12).  r is the phase
+// Both updates read the state of the previous step (the Euler update of Alg. 1).  r is the phase
 // wrapped to [-pi, pi); the caller restores the range and counts windings.
 template <int M>
 __device__ __forceinline__ void step_f32(float &r, float &v, float n, float g, float dt, float A,

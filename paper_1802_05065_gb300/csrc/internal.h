@@ -18,7 +18,7 @@ const std::string &get_error();
 constexpr uint64_t kMaxSteps = 1ull << 48;
 constexpr int kMaxBins = 1 << 20;
 
-// A request decoded on the host (Alg. 1 lines 4-7 / Alg. 3 lines 5-9): double constants used
+// A request decoded on the host (the set-up of Alg. 1 / Alg. 3): double constants used
 // by the FP64 kernels and by the result arithmetic, and rounded single-precision constants
 // for the FP32 step.  Double quantities are evaluated in the order
 //   sigma = sqrt(((2 alpha) D) dt)  (underdamped)   sigma = sqrt((2 D) dt)  (overdamped)

@@ -198,3 +198,23 @@ def test_errors(lib):
             eng.poll(rid)
         c = eng.counters()
         assert c["resident_requests"] == 0
+
+
+def test_fair_share_no_starvation(lib):
+    """A request that never finishes (no noise, trapped) must not starve a short request
+    submitted after it: lanes are shared with an exact per-request cap."""
+    trapped = workloads.scaled(CONST_UNDER, D=0.0, max_steps=2**40)
+    with _engine(lib, chunk_steps=4096) as eng:
+        hog = eng.submit(lib_params(trapped), 2**22, 1)
+        eng.step(1)
+        short = eng.submit(lib_params(CONST_OVER), 20000, 2)
+        for _ in range(80):
+            eng.step(1)
+            st, res = eng.poll(short)
+            if st == 0:
+                break
+        assert st == 0, "short request starved behind a never-ending one"
+        c = eng.counters()
+        assert c["escapes"] >= res.n_escaped > 0
+        assert 0 < c["useful_steps"] <= c["lane_step_slots"]
+        eng.release(hog)
