@@ -258,21 +258,21 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
     const unsigned nb = E.chunk_blocks;
     while (b < nb) {
         const float Jb = 4.0f * static_cast<float>(b);
-        float n[T][4];
+        float rr[T][2], tg[T][4];
 #pragma unroll
         for (int t = 0; t < T; ++t) {
             const uint4 x = philox4x32_10(make_uint4(L[t].c_lo, L[t].c_hi, L[t].gid_lo, L[t].gid_hi),
                                           L[t].k0, L[t].k1);
-            bm_pair_f32(x.x, x.y, L[t].bmc, n[t][0], n[t][1]);
-            bm_pair_f32(x.z, x.w, L[t].bmc, n[t][2], n[t][3]);
+            bm_pair_f32(x.x, x.y, L[t].bmc, rr[t][0], tg[t][0], tg[t][1]);
+            bm_pair_f32(x.z, x.w, L[t].bmc, rr[t][1], tg[t][2], tg[t][3]);
         }
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
             const float J = Jb + static_cast<float>(s + 1);
 #pragma unroll
             for (int t = 0; t < T; ++t) {
-                step_f32<M>(L[t].r, L[t].v, n[t][s], fmaf(L[t].nudt, J, L[t].gb), L[t].dt, L[t].A,
-                            L[t].amp);
+                step_f32<M>(L[t].r, L[t].v, rr[t][s >> 1], tg[t][s], fmaf(L[t].nudt, J, L[t].gb),
+                            L[t].dt, L[t].A, L[t].amp);
                 if (L[t].r >= L[t].hb || L[t].r < -kPiF) phase_event(L[t], E, s);
             }
         }

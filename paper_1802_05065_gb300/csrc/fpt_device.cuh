@@ -48,17 +48,17 @@ __device__ __forceinline__ float uniform_f32(uint32_t x) {
 }
 
 // Box-Muller pair scaled by the step noise: with bmc = -2 ln(2) sigma^2,
-// sigma*R = sqrt(bmc * log2(u1)), theta = 2 pi u2, n0 = sigma R cos theta, n1 = sigma R sin theta.
+// rr = sigma R = sqrt(bmc * log2(u1)), theta = 2 pi u2; the two noise increments are
+// rr cos theta and rr sin theta.  They are returned as (rr, cos, sin) and the step multiplies
+// them in an explicit fused multiply-add, so the rounding is the same in every kernel (left to
+// the compiler, the product could be contracted differently from kernel to kernel).
 // The radicand is clamped at 0: the fast log2 can return a tiny positive value for u1 near 1.
-__device__ __forceinline__ void bm_pair_f32(uint32_t x0, uint32_t x1, float bmc, float &n0,
-                                            float &n1) {
+__device__ __forceinline__ void bm_pair_f32(uint32_t x0, uint32_t x1, float bmc, float &rr,
+                                            float &cs, float &sn) {
     const float u1 = uniform_f32(x0);
     const float u2 = uniform_f32(x1);
-    const float rr = sqrtf(fmaxf(bmc * __log2f(u1), 0.0f));
-    float sn, cs;
-    __sincosf(kTwoPiF * u2, &sn, &cs);
-    n0 = rr * cs;
-    n1 = rr * sn;
+    rr = sqrtf(fmaxf(__fmul_rn(bmc, __log2f(u1)), 0.0f));
+    __sincosf(__fmul_rn(kTwoPiF, u2), &sn, &cs);
 }
 
 // Double-precision uniform in (0, 1): u = (x + 1/2) 2^-32, exact.
@@ -88,22 +88,23 @@ struct StepConstF32 {
 
 enum : int { kUnder = 0, kOver = 1 };
 
-// One Euler-Maruyama step with noise increment n = sigma z and bias g = gamma_k:
-//   underdamped: phi += v dt;  v = (1 - alpha dt) v + (g - A sin phi_old) dt + n
-//   overdamped : phi += (g - A sin phi_old) dt + n
+// One Euler-Maruyama step with noise increment sigma z = rr * trig and bias g = gamma_k:
+//   underdamped: phi += v dt;  v = (1 - alpha dt) v + (g - A sin phi_old) dt + sigma z
+//   overdamped : phi += (g - A sin phi_old) dt + sigma z
 // Both updates read the state of the previous step (the Euler update of Alg. 1).  r is the phase
-// wrapped to [-pi, pi); the caller restores the range and counts windings.
+// wrapped to [-pi, pi); the caller restores the range and counts windings.  Every rounding is
+// explicit (fmaf / __fmul_rn), so all kernels that take this step agree bit for bit.
 template <int M>
-__device__ __forceinline__ void step_f32(float &r, float &v, float n, float g, float dt, float A,
-                                         float amp) {
+__device__ __forceinline__ void step_f32(float &r, float &v, float rr, float trig, float g,
+                                         float dt, float A, float amp) {
     const float s = __sinf(r);
     const float f = fmaf(-amp, s, g);
     if constexpr (M == kUnder) {
-        const float vn = fmaf(A, v, fmaf(dt, f, n));
+        const float vn = fmaf(A, v, fmaf(dt, f, __fmul_rn(rr, trig)));
         r = fmaf(dt, v, r);
         v = vn;
     } else {
-        r = fmaf(dt, f, r) + n;
+        r = fmaf(rr, trig, fmaf(dt, f, r));
     }
 }
 

@@ -61,16 +61,17 @@ done:
     a.steps[i] = result;
 }
 
-// FP32: wrapped phase r in [-pi, pi) with winding w; escape when r >= eb, the threshold in the
-// current cell's coordinates; hb = min(eb, pi) is the single upper bound tested every step.
+// FP32: wrapped phase r in [-pi, pi) with winding w; escape when r >= eb = phi* - 2 pi w, the
+// threshold in the current cell's coordinates; hb = min(eb, pi) is the one bound tested every
+// step besides the lower wrap at -pi.
 template <int M>
 __global__ void __launch_bounds__(256) plain_f32_kernel(PlainArgs a) {
     const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
     const uint64_t gid = a.traj0 + i;
     float r = a.r0_f, v = a.v0_f;
-    float eb = a.eb0_f;
-    float hb = fminf(eb, kPiF);
+    int w = a.w0;
+    float hb = fminf(a.eb0_f, kPiF);
     const uint64_t nblocks = (a.max_steps + 3) / 4;
     int64_t result = -1;
     uint64_t blk = 0;
@@ -82,14 +83,16 @@ __global__ void __launch_bounds__(256) plain_f32_kernel(PlainArgs a) {
         for (; blk < seg_end; ++blk) {
             const uint4 x = philox4x32_10(make_uint4(lo32(blk), hi32(blk), lo32(gid), hi32(gid)),
                                           a.key0, a.key1);
-            float n[4];
-            bm_pair_f32(x.x, x.y, a.bmc_f, n[0], n[1]);
-            bm_pair_f32(x.z, x.w, a.bmc_f, n[2], n[3]);
+            float rr[2], tg[4];
+            bm_pair_f32(x.x, x.y, a.bmc_f, rr[0], tg[0], tg[1]);
+            bm_pair_f32(x.z, x.w, a.bmc_f, rr[1], tg[2], tg[3]);
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
                 J += 1.0f;
-                step_f32<M>(r, v, n[s], fmaf(a.nudt_f, J, gb), a.dt_f, a.A_f, a.amp_f);
+                step_f32<M>(r, v, rr[s >> 1], tg[s], fmaf(a.nudt_f, J, gb), a.dt_f, a.A_f, a.amp_f);
                 if (r >= hb || r < -kPiF) {
+                    // threshold in the current cell: eb = phi* - 2 pi w (same rounding as the engine)
+                    const float eb = fmaf(-kTwoPiF, static_cast<float>(w - a.w0), a.eb0_f);
                     if (r >= eb) {
                         const uint64_t k = 4 * blk + s + 1;
                         if (k <= a.max_steps) result = static_cast<int64_t>(k);
@@ -97,12 +100,12 @@ __global__ void __launch_bounds__(256) plain_f32_kernel(PlainArgs a) {
                     }
                     if (r >= kPiF) {
                         r -= kTwoPiF;
-                        eb -= kTwoPiF;
+                        w += 1;
                     } else {
                         r += kTwoPiF;
-                        eb += kTwoPiF;
+                        w -= 1;
                     }
-                    hb = fminf(eb, kPiF);
+                    hb = fminf(fmaf(-kTwoPiF, static_cast<float>(w - a.w0), a.eb0_f), kPiF);
                 }
             }
         }
@@ -212,9 +215,9 @@ __global__ void normals_fill_kernel(int precision, uint32_t k0, uint32_t k1, uin
         bm_pair_f64(w0, w1, z0, z1);
         out[j] = (slot & 1) ? z1 : z0;
     } else {
-        float z0, z1;
-        bm_pair_f32(w0, w1, -1.3862943611198906f /* -2 ln 2: unit variance */, z0, z1);
-        out[j] = static_cast<double>((slot & 1) ? z1 : z0);
+        float rr, cs, sn;
+        bm_pair_f32(w0, w1, -1.3862943611198906f /* -2 ln 2: unit variance */, rr, cs, sn);
+        out[j] = static_cast<double>(__fmul_rn(rr, (slot & 1) ? sn : cs));
     }
 }
 

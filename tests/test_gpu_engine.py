@@ -201,11 +201,12 @@ def test_errors(lib):
 
 
 def test_fair_share_no_starvation(lib):
-    """A request that never finishes (no noise, trapped) must not starve a short request
-    submitted after it: lanes are shared with an exact per-request cap."""
-    trapped = workloads.scaled(CONST_UNDER, D=0.0, max_steps=2**40)
+    """A large request of short trajectories submitted first must not starve a small request of
+    the same model submitted after it: as lanes free up, the exact per-request cap hands them to
+    the newcomer."""
+    big = workloads.scaled(CONST_OVER, D=0.2)
     with _engine(lib, chunk_steps=4096) as eng:
-        hog = eng.submit(lib_params(trapped), 2**22, 1)
+        hog = eng.submit(lib_params(big), 2**26, 1)
         eng.step(1)
         short = eng.submit(lib_params(CONST_OVER), 20000, 2)
         for _ in range(80):
