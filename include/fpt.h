@@ -204,6 +204,34 @@ const char *fpt_last_error(fpt_engine *e);
 const char *fpt_status_string(fpt_status s);
 
 /* ------------------------------------------------------------------------------------------
+ * Allocation-free run (the paper has no counterpart; this is a library convenience).
+ *
+ * For callers that cannot allocate device memory while they run: a host program that has
+ * already reserved the device memory for its own pool, code in a latency-critical loop where
+ * cudaMalloc's implicit synchronisation is not acceptable, or a plugin host whose contract
+ * forbids allocation during execution.  It integrates one request (FP32, same arithmetic as
+ * fpt_plain_launch with precision FPT_FP32) with lanes that take the next trajectory as soon as
+ * theirs finishes, all in ONE launch that runs until every trajectory has finished, and calls
+ * no cudaMalloc / cudaFree or allocating library routine.
+ *
+ * Scratch: a fixed 8 MiB __device__ array inside the library (every GPU that loads the library
+ * holds it until the process exits): a queue head, a finished-CTA counter and one record of
+ * partial sums and per-bin counts per CTA.  Requests whose records do not fit (many histogram
+ * bins: roughly bins > 8 MiB / (4 x CTAs), or bins > 10240) are rejected with FPT_EINVAL and a
+ * message giving the limit.  The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call before any stream
+ * capture.  Every call shares the array: the header is cleared on `stream` before each launch,
+ * and calls that overlap on the GPU (other streams, other threads) race on it.
+ *
+ * Arguments: params as for the engine but stop_rse must be 0; trajectories params->traj_offset
+ * .. +n_traj-1 of `seed`.  d_steps (device, n_traj int64, may be NULL) receives each escape step
+ * or -1; d_sums (one fpt_sums) and d_hist (params->hist_bins uint64) are ACCUMULATED into:
+ * zero them first.  Enqueued on `stream`; returns without waiting.
+ * ------------------------------------------------------------------------------------------ */
+fpt_status fpt_run_noalloc(const fpt_params *params, uint64_t n_traj, uint64_t seed,
+                           int64_t *d_steps, fpt_sums *d_sums, uint64_t *d_hist, void *stream);
+
+/* ------------------------------------------------------------------------------------------
  * Random-number hooks (device buffers), for checking the device generator against the oracle.
  * ------------------------------------------------------------------------------------------ */
 

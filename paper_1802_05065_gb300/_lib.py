@@ -88,7 +88,7 @@ EXPORTS = [
     "fpt_step", "fpt_poll", "fpt_wait", "fpt_histogram", "fpt_per_traj", "fpt_per_traj_steps",
     "fpt_release", "fpt_get_counters", "fpt_engine_stream", "fpt_destroy", "fpt_last_error",
     "fpt_status_string", "fpt_philox_fill", "fpt_normals_fill", "fpt_version",
-    "fpt_request_sums",
+    "fpt_request_sums", "fpt_run_noalloc",
 ]
 
 _lib = None
@@ -116,6 +116,7 @@ def load() -> ctypes.CDLL:
     L.fpt_histogram.argtypes = [vp, u64, P(u64), i32, P(u64), P(u64)]
     L.fpt_per_traj.argtypes = [vp, u64, P(f64), u64]
     L.fpt_request_sums.argtypes = [vp, u64, P(Sums)]
+    L.fpt_run_noalloc.argtypes = [P(Params), u64, u64, vp, vp, vp, vp]
     L.fpt_per_traj_steps.argtypes = [vp, u64, P(ctypes.c_int64), u64]
     L.fpt_release.argtypes = [vp, u64]
     L.fpt_get_counters.argtypes = [vp, P(EngineCounters)]
@@ -132,7 +133,8 @@ def load() -> ctypes.CDLL:
     for name in ("fpt_plain_launch", "fpt_reduce_steps", "fpt_sums_finish", "fpt_create",
                  "fpt_submit", "fpt_step", "fpt_poll", "fpt_wait", "fpt_histogram",
                  "fpt_per_traj", "fpt_per_traj_steps", "fpt_release", "fpt_get_counters",
-                 "fpt_destroy", "fpt_philox_fill", "fpt_normals_fill", "fpt_request_sums"):
+                 "fpt_destroy", "fpt_philox_fill", "fpt_normals_fill", "fpt_request_sums",
+                 "fpt_run_noalloc"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -196,6 +198,12 @@ def philox_fill(seed: int, traj: int, block0: int, nblocks: int, d_out: int, str
 def normals_fill(precision: int, seed: int, traj: int, n0: int, n: int, d_out: int,
                  stream: int = 0):
     _check(load().fpt_normals_fill(precision, seed, traj, n0, n, d_out, stream))
+
+
+def run_noalloc(p: Params, n_traj: int, seed: int, d_steps: int, d_sums: int, d_hist: int,
+                stream: int = 0):
+    """fpt_run_noalloc: one request in one launch, no device allocation (see include/fpt.h)."""
+    _check(load().fpt_run_noalloc(ctypes.byref(p), n_traj, seed, d_steps, d_sums, d_hist, stream))
 
 
 def version() -> str:

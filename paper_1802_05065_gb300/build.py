@@ -27,7 +27,7 @@ COMMON = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC,-ffp-contract=o
           "-I", CSRC, "-I", INCLUDE]
 # single-precision hot path: flush denormals, approximate sqrt / division (MUFU)
 FAST32 = ["--ftz=true", "--prec-sqrt=false", "--prec-div=false"]
-ENGINE_UNITS = ["common.cpp", "plain.cu", "engine_kernels.cu", "engine.cpp"]
+ENGINE_UNITS = ["common.cpp", "plain.cu", "engine_kernels.cu", "engine.cpp", "noalloc.cu"]
 
 
 def nvcc() -> str:
