@@ -152,6 +152,7 @@ typedef struct {
     uint32_t grid, block, traj_per_thread, chunk_steps;
     uint32_t resident_requests, pending_requests;
     double kernel_ms;           /* summed device time of the resident-kernel launches (CUDA events) */
+    uint64_t preempted;         /* lane suspensions ordered so starved requests get their share */
 } fpt_engine_counters;
 
 /* Create an engine on config->device (NULL config = defaults). */

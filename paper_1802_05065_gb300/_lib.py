@@ -77,6 +77,7 @@ class EngineCounters(ctypes.Structure):
         ("block", ctypes.c_uint32), ("traj_per_thread", ctypes.c_uint32),
         ("chunk_steps", ctypes.c_uint32), ("resident_requests", ctypes.c_uint32),
         ("pending_requests", ctypes.c_uint32), ("kernel_ms", ctypes.c_double),
+        ("preempted", ctypes.c_uint64),
     ]
 
     def as_dict(self) -> dict:

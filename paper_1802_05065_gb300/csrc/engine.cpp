@@ -50,6 +50,8 @@ struct Request {
     IdBlockAcc *acc = nullptr;
     unsigned *hist = nullptr;
     long long *per_traj = nullptr;
+    ParkEntry *park = nullptr;
+    uint32_t park_cap = 0;
     size_t bytes = 0;
     uint32_t stop_block = 4096, n_idblocks = 0;
     unsigned prefix = 0;
@@ -58,9 +60,16 @@ struct Request {
     Clock::time_point t_submit;
 };
 
-size_t request_bytes(const fpt_params &p, uint64_t n_traj, uint32_t B) {
+// Ring of suspended trajectories: never more than the lanes can hold twice over.
+uint32_t park_capacity(uint64_t n_traj, unsigned lanes) {
+    const uint64_t cap = std::min<uint64_t>(n_traj, 2ull * lanes);
+    return static_cast<uint32_t>(std::max<uint64_t>(cap, 1));
+}
+
+size_t request_bytes(const fpt_params &p, uint64_t n_traj, uint32_t B, unsigned lanes) {
     const uint64_t nb = (n_traj + B - 1) / B;
     size_t bytes = nb * sizeof(IdBlockAcc) + nb * static_cast<size_t>(p.hist_bins) * 4;
+    bytes += static_cast<size_t>(park_capacity(n_traj, lanes)) * sizeof(ParkEntry);
     if (p.keep_per_traj) bytes += n_traj * 8;
     return bytes;
 }
@@ -78,6 +87,7 @@ struct fpt_engine {
     SlotDev *d_slots = nullptr;
     SlotCtl *d_ctl = nullptr;
     int *d_caps = nullptr, *d_act = nullptr, *d_act_count = nullptr;
+    int *d_preempt = nullptr, *d_vacate = nullptr, *d_strict = nullptr;
     void *d_lane_mem = nullptr;
     int *d_warp_kind = nullptr;
     unsigned *d_warp_cursor = nullptr;
@@ -87,6 +97,8 @@ struct fpt_engine {
     SlotDev *h_slots = nullptr;
     SlotCtl *h_ctl = nullptr, *h_ctl_init = nullptr;
     int *h_caps = nullptr, *h_act = nullptr, *h_act_count = nullptr;
+    int *h_preempt = nullptr, *h_flags = nullptr;   // flags: vacate[2], strict
+    uint64_t preempted = 0;
     unsigned long long *h_counters = nullptr;
     int *h_state = nullptr;
     // resident-kernel timing (events around the chunk kernel, recorded inside the graph)
@@ -138,9 +150,11 @@ void free_request_buffers(Request &R, fpt_engine *e) {
     if (R.acc) cudaFree(R.acc);
     if (R.hist) cudaFree(R.hist);
     if (R.per_traj) cudaFree(R.per_traj);
+    if (R.park) cudaFree(R.park);
     R.acc = nullptr;
     R.hist = nullptr;
     R.per_traj = nullptr;
+    R.park = nullptr;
     e->mem_used -= R.bytes;
     R.bytes = 0;
 }
@@ -161,7 +175,7 @@ fpt_status admit(fpt_engine *e) {
                 break;
             }
         if (s < 0) break;
-        const size_t bytes = request_bytes(R.params, R.n_traj, R.stop_block);
+        const size_t bytes = request_bytes(R.params, R.n_traj, R.stop_block, e->lanes);
         if (e->mem_used + bytes > e->budget) {
             ++it;
             continue;
@@ -175,6 +189,8 @@ fpt_status admit(fpt_engine *e) {
             CK(cudaMalloc(&R.per_traj, R.n_traj * 8));
             CK(cudaMemsetAsync(R.per_traj, 0xFF, R.n_traj * 8, e->stream));
         }
+        R.park_cap = park_capacity(R.n_traj, e->lanes);
+        CK(cudaMalloc(&R.park, static_cast<size_t>(R.park_cap) * sizeof(ParkEntry)));
         R.bytes = bytes;
         e->mem_used += bytes;
         const Decoded &d = R.dec;
@@ -211,6 +227,8 @@ fpt_status admit(fpt_engine *e) {
         S.acc = R.acc;
         S.hist = R.hist;
         S.per_traj = R.per_traj;
+        S.park = R.park;
+        S.park_cap = R.park_cap;
         CK(cudaMemcpyAsync(e->d_slots + s, &S, sizeof(SlotDev), cudaMemcpyHostToDevice, e->stream));
         SlotCtl &C = e->h_ctl_init[s];
         std::memset(&C, 0, sizeof(C));
@@ -224,10 +242,17 @@ fpt_status admit(fpt_engine *e) {
     return FPT_OK;
 }
 
+// Claimable lists, fair-share caps and preemption orders for the next launch (mu held).
+// Fair share = lanes / running requests.  A request is starved when it has work (unclaimed
+// ids or suspended trajectories) and holds less than half of min(share, its demand).  While
+// anyone is starved: caps are strict, requests above their share suspend the excess lanes at
+// the end of the launch, and if a starved request's model differs, whole warps of the other
+// model vacate so they can switch.
 void build_lists(fpt_engine *e) {
     int cnt[2] = {0, 0};
     int active = 0;
     for (int s = 0; s < e->maxr; ++s) {
+        e->h_preempt[s] = 0;
         if (!e->slot_req[s]) continue;
         Request &R = *e->reqs[e->slot_req[s]];
         if (R.phase != kRunning) continue;
@@ -236,8 +261,41 @@ void build_lists(fpt_engine *e) {
     }
     e->h_act_count[0] = cnt[0];
     e->h_act_count[1] = cnt[1];
-    const int cap = active ? static_cast<int>((e->lanes + active - 1) / active) + 32 : 0;
+    const int share = active ? static_cast<int>((e->lanes + active - 1) / active) : 0;
+    const int cap = active ? share + 32 : 0;
     for (int s = 0; s < e->maxr; ++s) e->h_caps[s] = cap;
+    e->h_flags[0] = e->h_flags[1] = e->h_flags[2] = 0;
+    if (active < 2) return;
+    int64_t deficit[2] = {0, 0};
+    bool over[2] = {false, false};
+    for (int s = 0; s < e->maxr; ++s) {
+        if (!e->slot_req[s]) continue;
+        Request &R = *e->reqs[e->slot_req[s]];
+        if (R.phase != kRunning) continue;
+        const SlotCtl &C = e->h_ctl[s];
+        if (C.state != kSlotActive) continue;     // not yet launched or finishing
+        const int64_t unclaimed = C.head < R.n_traj ? static_cast<int64_t>(R.n_traj - C.head) : 0;
+        const int64_t remaining = unclaimed + std::max(C.park_avail, 0);
+        const int64_t want = std::min<int64_t>(share, C.inflight + remaining);
+        if (remaining > 0 && C.inflight < want / 2) deficit[R.dec.model] += want - C.inflight;
+        if (C.inflight > share) over[R.dec.model] = true;
+    }
+    if (deficit[0] + deficit[1] == 0) return;
+    e->h_flags[2] = 1;   // strict caps
+    for (int s = 0; s < e->maxr; ++s) {
+        if (!e->slot_req[s]) continue;
+        Request &R = *e->reqs[e->slot_req[s]];
+        if (R.phase != kRunning) continue;
+        const SlotCtl &C = e->h_ctl[s];
+        if (C.state != kSlotActive || C.inflight <= share) continue;
+        const int room = static_cast<int>(R.park_cap) - std::max(C.park_used, 0);
+        e->h_preempt[s] = std::max(0, std::min(C.inflight - share, room));
+        e->preempted += static_cast<uint64_t>(e->h_preempt[s]);
+    }
+    const int64_t lanes_per_warp = 32ll * e->T;
+    for (int m = 0; m < 2; ++m)
+        if (deficit[1 - m] > 0 && over[m])
+            e->h_flags[m] = static_cast<int>((deficit[1 - m] + lanes_per_warp - 1) / lanes_per_warp);
 }
 
 fpt_status enqueue_iteration(fpt_engine *e) {
@@ -246,6 +304,8 @@ fpt_status enqueue_iteration(fpt_engine *e) {
         return FPT_OK;
     }
     CK(cudaMemcpyAsync(e->d_caps, e->h_caps, e->maxr * sizeof(int), cudaMemcpyHostToDevice, e->stream));
+    CK(cudaMemcpyAsync(e->d_preempt, e->h_preempt, e->maxr * sizeof(int), cudaMemcpyHostToDevice, e->stream));
+    CK(cudaMemcpyAsync(e->d_vacate, e->h_flags, 3 * sizeof(int), cudaMemcpyHostToDevice, e->stream));
     CK(cudaMemcpyAsync(e->d_act, e->h_act, 2 * e->maxr * sizeof(int), cudaMemcpyHostToDevice, e->stream));
     CK(cudaMemcpyAsync(e->d_act_count, e->h_act_count, 2 * sizeof(int), cudaMemcpyHostToDevice, e->stream));
     const unsigned evflags = e->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
@@ -386,6 +446,8 @@ void destroy_all(fpt_engine *e) {
     cudaFree(e->d_caps);
     cudaFree(e->d_act);
     cudaFree(e->d_act_count);
+    cudaFree(e->d_preempt);
+    cudaFree(e->d_vacate);
     cudaFree(e->d_lane_mem);
     cudaFree(e->d_warp_kind);
     cudaFree(e->d_warp_cursor);
@@ -396,6 +458,8 @@ void destroy_all(fpt_engine *e) {
     cudaFreeHost(e->h_caps);
     cudaFreeHost(e->h_act);
     cudaFreeHost(e->h_act_count);
+    cudaFreeHost(e->h_preempt);
+    cudaFreeHost(e->h_flags);
     cudaFreeHost(e->h_counters);
     if (e->ev_k0) cudaEventDestroy(e->ev_k0);
     if (e->ev_k1) cudaEventDestroy(e->ev_k1);
@@ -447,6 +511,10 @@ fpt_status create_impl(const fpt_engine_config *cfg_in, fpt_engine *e) {
     CK(cudaMalloc(&e->d_caps, R * sizeof(int)));
     CK(cudaMalloc(&e->d_act, 2 * R * sizeof(int)));
     CK(cudaMalloc(&e->d_act_count, 2 * sizeof(int)));
+    CK(cudaMalloc(&e->d_preempt, R * sizeof(int)));
+    CK(cudaMalloc(&e->d_vacate, 3 * sizeof(int)));   // vacate[2], strict
+    CK(cudaMemsetAsync(e->d_preempt, 0, R * sizeof(int), e->stream));
+    CK(cudaMemsetAsync(e->d_vacate, 0, 3 * sizeof(int), e->stream));
     const size_t L = e->lanes;
     CK(cudaMalloc(&e->d_lane_mem, L * 4 * 10));
     const unsigned nwarps = static_cast<unsigned>(e->grid) * e->block / 32;
@@ -482,6 +550,10 @@ fpt_status create_impl(const fpt_engine_config *cfg_in, fpt_engine *e) {
     CK(cudaMallocHost(&e->h_caps, R * sizeof(int)));
     CK(cudaMallocHost(&e->h_act, 2 * R * sizeof(int)));
     CK(cudaMallocHost(&e->h_act_count, 2 * sizeof(int)));
+    CK(cudaMallocHost(&e->h_preempt, R * sizeof(int)));
+    CK(cudaMallocHost(&e->h_flags, 3 * sizeof(int)));
+    std::memset(e->h_preempt, 0, R * sizeof(int));
+    std::memset(e->h_flags, 0, 3 * sizeof(int));
     CK(cudaMallocHost(&e->h_counters, kCntCount * sizeof(unsigned long long)));
     std::memset(e->h_ctl, 0, R * sizeof(SlotCtl));
     std::memset(e->h_caps, 0, R * sizeof(int));
@@ -494,6 +566,9 @@ fpt_status create_impl(const fpt_engine_config *cfg_in, fpt_engine *e) {
     d.ctl = e->d_ctl;
     d.caps = e->d_caps;
     d.act_list = e->d_act;
+    d.preempt = e->d_preempt;
+    d.vacate = e->d_vacate;
+    d.strict = e->d_vacate + 2;
     d.act_count = e->d_act_count;
     d.warp_kind = e->d_warp_kind;
     d.warp_cursor = e->d_warp_cursor;
@@ -549,7 +624,7 @@ extern "C" fpt_status fpt_submit(fpt_engine *e, const fpt_params *params, uint64
     const uint64_t nb = (n_traj + R->stop_block - 1) / R->stop_block;
     if (nb > 0xFFFFFFFFull) return fail(e, FPT_EINVAL, "too many id blocks");
     R->n_idblocks = static_cast<uint32_t>(nb);
-    if (request_bytes(*params, n_traj, R->stop_block) > e->budget)
+    if (request_bytes(*params, n_traj, R->stop_block, e->lanes) > e->budget)
         return fail(e, FPT_ENOMEM, "request larger than the engine's memory budget");
     R->t_submit = Clock::now();
     {
@@ -752,6 +827,7 @@ extern "C" fpt_status fpt_get_counters(fpt_engine *e, fpt_engine_counters *out) 
     out->traj_per_thread = e->T;
     out->chunk_steps = e->chunk_blocks * 4;
     out->kernel_ms = e->kernel_ms;
+    out->preempted = e->preempted;
     for (int s = 0; s < e->maxr; ++s)
         if (e->slot_req[s]) ++out->resident_requests;
     out->pending_requests = static_cast<uint32_t>(e->pending.size());

@@ -17,6 +17,19 @@ namespace fpt {
 
 enum : int { kSlotFree = 0, kSlotActive = 1, kSlotFinished = 2, kSlotCancelled = 3 };
 
+// Blocks (of 4 steps) between re-bases of a trajectory's single-precision bias: gamma_k is
+// formed as gs + nu dt (s + 1) with gs = gb + nu dt Jf and gb = gamma0 + nu dt 4 c_base in FP64,
+// c_base the trajectory's own block count rounded down to a multiple of kRebaseBlocks, so the
+// rounding depends only on the trajectory's step count, never on scheduling.
+constexpr unsigned kRebaseBlocks = 1u << 20;
+
+// A trajectory suspended by preemption: everything needed to continue it exactly.
+struct ParkEntry {
+    float r, v;
+    int w;
+    unsigned c_lo, c_hi, gid_lo, gid_hi, pad;
+};
+
 // Exact accumulators of one block of stop_block consecutive trajectory ids.
 struct IdBlockAcc {
     unsigned int done, escaped, under, over;
@@ -41,6 +54,8 @@ struct SlotDev {
     IdBlockAcc *acc;
     unsigned int *hist;
     long long *per_traj;
+    ParkEntry *park;           // ring of suspended trajectories
+    unsigned park_cap;
 };
 
 struct SlotCtl {
@@ -50,6 +65,11 @@ struct SlotCtl {
     unsigned int prefix;       // id blocks folded into the running sums
     unsigned int reserved;
     unsigned long long n_done, n_esc, s1_lo, s1_hi, s2_lo, s2_hi, under, over;
+    // suspended-trajectory ring: pushes at launch end, committed by the scan, popped by refill
+    unsigned park_tail, park_head, park_commit;
+    int park_avail;            // committed entries not yet taken
+    int park_used;             // entries pushed and not yet taken (bounds the ring)
+    int reserved2;
 };
 
 struct LaneSoA {
@@ -64,6 +84,9 @@ struct EngineDev {
     SlotDev *slots;
     SlotCtl *ctl;
     const int *caps;        // [max_requests] fair-share lane caps
+    int *preempt;           // [max_requests] lanes to suspend at the end of this launch
+    int *vacate;            // [2] whole warps of each model to suspend at the end of this launch
+    const int *strict;      // [1] 1: never exceed the caps (someone is starved)
     const int *act_list;    // [2][max_requests] claimable slots per model
     const int *act_count;   // [2]
     LaneSoA lanes;

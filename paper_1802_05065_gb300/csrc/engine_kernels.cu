@@ -2,11 +2,17 @@
 //
 // One launch ("chunk") advances every resident lane by up to chunk_blocks x 4 Euler-Maruyama
 // steps.  A lane integrates one trajectory: Philox4x32-10 -> Box-Muller -> step (Alg. 1 / 3)
-// on a phase wrapped to [-pi, pi) with an integer winding count.  Escape and wrap events are
-// caught by one compare per step (r >= hb || r < -pi); at the end of each 4-step block the warp
-// votes, finished lanes publish their exact result and the warp refills them from the
-// requests' work queues (warp-aggregated atomicAdd on the queue head), so lanes never wait for
-// the slowest trajectory of a batch (the dynamic job assignment of Sec. III.B, Fig. 6).
+// on a phase wrapped to [-pi, pi) with an integer winding count.  Escape and upper-wrap events
+// are caught by one compare per step (r >= hb); the lower wrap (r < -pi) is applied at the end
+// of each 4-step block.  At the block end the warp votes, finished lanes publish their exact
+// result and the warp refills them -- first with suspended trajectories, then with new ids from
+// the requests' work queues (warp-aggregated atomics) -- so lanes never wait for the slowest
+// trajectory of a batch (the dynamic job assignment of Sec. III.B, Fig. 6).
+//
+// Preemption: at the end of a launch, lanes of requests above their fair share may suspend
+// their trajectory into the request's ring (state r, v, w, step count, id); a later refill
+// resumes it exactly.  The ramped bias is formed from the trajectory's own step count, so a
+// trajectory's arithmetic never depends on which lane, launch or schedule ran it.
 //
 // A warp integrates one model at a time (underdamped or overdamped code path); the request of
 // each lane is free, so requests of the same model share warps.  Refill is round-robin over
@@ -27,8 +33,10 @@ constexpr unsigned kFull = 0xFFFFFFFFu;
 struct Lane {
     float r, v, hb;
     int w, slot, esc;
-    unsigned c_lo, c_hi, gid_lo, gid_hi, budget;
-    float dt, A, amp, bmc, nudt, gb;
+    unsigned c_lo, c_hi, gid_lo, gid_hi;
+    unsigned budget;      // blocks to the next event: step budget end or bias re-base
+    float gb, Jf;         // bias base and 4 x blocks since the base (exact)
+    float dt, A, amp, bmc, nudt;
     unsigned k0, k1;
 };
 
@@ -46,7 +54,7 @@ __device__ __forceinline__ void set_idle(Lane &L) {
     L.hb = 0.0f;
     L.esc = -1;
     L.budget = 0xFFFFFFFFu;
-    L.dt = L.A = L.amp = L.bmc = L.nudt = L.gb = 0.0f;
+    L.dt = L.A = L.amp = L.bmc = L.nudt = L.gb = L.Jf = 0.0f;
     L.k0 = L.k1 = 0;
 }
 
@@ -64,10 +72,25 @@ __device__ __forceinline__ void load_consts(Lane &L, const SlotDev *S) {
     L.k1 = S->key1;
 }
 
-// Start trajectory `idx` of request slot s at block b of this launch.  The single-precision
-// bias base gb is set so that gb + nudt * J equals gamma0 + nu dt k for this lane's step k,
-// with J = 4 b + (step within block) + 1 counted from the start of the launch.
-__device__ __forceinline__ void init_lane(Lane &L, const EngineDev &E, int s, unsigned long long idx, unsigned b) {
+__device__ __forceinline__ unsigned long long lane_c(const Lane &L) {
+    return (static_cast<unsigned long long>(L.c_hi) << 32) | L.c_lo;
+}
+
+// Bias base and event countdown from the trajectory's block count c:
+// gb = gamma0 + nu dt 4 c_base (FP64, rounded once), Jf = 4 (c - c_base),
+// budget = blocks until the step budget ends or the next re-base, whichever is first.
+__device__ __forceinline__ void set_progress(Lane &L, const SlotDev *S) {
+    const unsigned long long c = lane_c(L);
+    const unsigned long long cb = c - (c % kRebaseBlocks);
+    L.gb = static_cast<float>(S->gamma0 + S->nudt_d * static_cast<double>(4ull * cb));
+    L.Jf = static_cast<float>(4ull * (c - cb));
+    const unsigned long long to_end = S->nblocks > c ? S->nblocks - c : 0ull;
+    const unsigned long long to_base = kRebaseBlocks - (c - cb);
+    L.budget = static_cast<unsigned>(to_end < to_base ? to_end : to_base);
+}
+
+// Start trajectory `idx` of request slot s.
+__device__ __forceinline__ void init_lane(Lane &L, const EngineDev &E, int s, unsigned long long idx) {
     const SlotDev *S = E.slots + s;
     const unsigned long long gid = S->traj_offset + idx;
     L.slot = s;
@@ -79,9 +102,25 @@ __device__ __forceinline__ void init_lane(Lane &L, const EngineDev &E, int s, un
     L.w = S->w0;
     L.hb = fminf(S->eb0, kPiF);
     L.esc = -1;
-    L.budget = clamp_u32(S->nblocks);
     load_consts(L, S);
-    L.gb = static_cast<float>(S->gamma0 - S->nudt_d * static_cast<double>(4ull * b));
+    set_progress(L, S);
+}
+
+// Continue a suspended trajectory exactly where it stopped.
+__device__ __forceinline__ void resume_lane(Lane &L, const EngineDev &E, int s, const ParkEntry &P) {
+    const SlotDev *S = E.slots + s;
+    L.slot = s;
+    L.r = P.r;
+    L.v = P.v;
+    L.w = P.w;
+    L.c_lo = P.c_lo;
+    L.c_hi = P.c_hi;
+    L.gid_lo = P.gid_lo;
+    L.gid_hi = P.gid_hi;
+    L.hb = fminf(fmaf(-kTwoPiF, static_cast<float>(P.w - S->w0), S->eb0), kPiF);
+    L.esc = -1;
+    load_consts(L, S);
+    set_progress(L, S);
 }
 
 __device__ __forceinline__ void atomic_add128(unsigned long long *lo_p, unsigned long long *hi_p,
@@ -119,9 +158,9 @@ __device__ __forceinline__ void emit(const SlotDev *S, unsigned long long gid, b
     atomicAdd(&A->done, 1u);
 }
 
-// Rare per-lane path: the phase left [-pi, min(eb, pi)).  eb = phi* - 2 pi w is the threshold
-// in the current cell's coordinates.  Escape freezes the lane (NaN phase: no further events)
-// and records the step within the block; otherwise wrap and count a winding.
+// Rare per-lane path: the phase reached hb = min(eb, pi), where eb = phi* - 2 pi w is the
+// threshold in the current cell's coordinates.  Escape freezes the lane (NaN phase: no further
+// events) and records the step within the block; otherwise wrap upwards and count a winding.
 __device__ __forceinline__ void phase_event(Lane &L, const EngineDev &E, int s) {
     const SlotDev *S = E.slots + L.slot;
     const float eb0 = S->eb0;
@@ -132,14 +171,17 @@ __device__ __forceinline__ void phase_event(Lane &L, const EngineDev &E, int s) 
         L.r = qnan_f();
         return;
     }
-    if (L.r >= kPiF) {
-        L.r -= kTwoPiF;
-        L.w += 1;
-    } else {
-        L.r += kTwoPiF;
-        L.w -= 1;
-    }
+    L.r -= kTwoPiF;
+    L.w += 1;
     L.hb = fminf(fmaf(-kTwoPiF, static_cast<float>(L.w - w0), eb0), kPiF);
+}
+
+// Lower wrap, applied at block ends (sin is accurate a little below -pi in between).
+__device__ __forceinline__ void wrap_down(Lane &L, const EngineDev &E) {
+    const SlotDev *S = E.slots + L.slot;
+    L.r += kTwoPiF;
+    L.w -= 1;
+    L.hb = fminf(fmaf(-kTwoPiF, static_cast<float>(L.w - S->w0), S->eb0), kPiF);
 }
 
 // Finish lanes that escaped in the last block or reached the step budget.
@@ -155,14 +197,11 @@ __device__ __forceinline__ void finish_lanes(Lane (&L)[T], const EngineDev &E, u
         const bool esc = L[t].esc >= 0;
         if (!esc && L[t].budget != 0) continue;
         const SlotDev *S = E.slots + L[t].slot;
-        const unsigned long long c = (static_cast<unsigned long long>(L[t].c_hi) << 32) | L[t].c_lo;
+        const unsigned long long c = lane_c(L[t]);
         const unsigned long long max_steps = S->max_steps;
-        if (!esc) {
-            const unsigned long long nb = S->nblocks;
-            if (c < nb) {   // the 32-bit budget had saturated: re-arm
-                L[t].budget = clamp_u32(nb - c);
-                continue;
-            }
+        if (!esc && c < S->nblocks) {   // re-base of the bias, not the end of the budget
+            set_progress(L[t], S);
+            continue;
         }
         unsigned long long k = 0;
         bool escaped = false;
@@ -184,8 +223,8 @@ __device__ __forceinline__ void finish_lanes(Lane (&L)[T], const EngineDev &E, u
 
 // Warp-collective refill of idle lanes with trajectories of requests of model `kind`.
 template <int T>
-__device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, int kind, unsigned b, int &n_active,
-                       unsigned &cursor) {
+__device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, int kind, int &n_active,
+                                       unsigned &cursor) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     unsigned idle[T];
@@ -199,18 +238,22 @@ __device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, int kin
     const int cnt = E.act_count[kind];
     if (cnt <= 0) return;
     const int *list = E.act_list + kind * E.max_requests;
-    for (int pass = 0; pass < 2 && total > 0; ++pass) {
+    const int passes = *E.strict ? 1 : 2;
+    for (int pass = 0; pass < passes && total > 0; ++pass) {
         for (int scanned = 0; scanned < cnt && total > 0; ++scanned) {
             const int s = list[cursor % static_cast<unsigned>(cnt)];
             ++cursor;
             unsigned long long base = 0;
-            int got = 0;
+            int got = 0, gp = 0;
+            unsigned p0 = 0;
             if (lane == 0) {
-                // Reserve in-flight places first (exact fair-share cap in the first pass), then
-                // claim ids from the queue head; unused reservations are given back.
+                // Reserve in-flight places first (exact fair-share cap in the first pass), take
+                // suspended trajectories, then new ids from the queue head; unused reservations
+                // are given back.
                 SlotCtl *C = E.ctl + s;
                 const unsigned long long n_traj = E.slots[s].n_traj;
-                if (vload(C->state) == kSlotActive && vload(C->head) < n_traj) {
+                if (vload(C->state) == kSlotActive &&
+                    (vload(C->head) < n_traj || vload(C->park_avail) > 0)) {
                     int want = total;
                     const int prev = atomicAdd(&C->inflight, want);
                     if (pass == 0) {
@@ -219,26 +262,45 @@ __device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, int kin
                         if (allowed < want) atomicSub(&C->inflight, want - allowed);
                         want = allowed;
                     }
-                    if (want > 0) {
-                        base = atomicAdd(&C->head, static_cast<unsigned long long>(want));
+                    if (want > 0 && vload(C->park_avail) > 0) {
+                        const int pv = atomicSub(&C->park_avail, want);
+                        if (pv <= 0) {
+                            atomicAdd(&C->park_avail, want);
+                        } else {
+                            gp = pv < want ? pv : want;
+                            if (gp < want) atomicAdd(&C->park_avail, want - gp);
+                            p0 = atomicAdd(&C->park_head, static_cast<unsigned>(gp));
+                            atomicSub(&C->park_used, gp);
+                        }
+                    }
+                    got = gp;
+                    if (want > gp && vload(C->head) < n_traj) {
+                        const int wn = want - gp;
+                        base = atomicAdd(&C->head, static_cast<unsigned long long>(wn));
                         if (base < n_traj) {
                             const unsigned long long left = n_traj - base;
-                            got = left < static_cast<unsigned long long>(want) ? static_cast<int>(left) : want;
+                            got += left < static_cast<unsigned long long>(wn) ? static_cast<int>(left) : wn;
                         }
-                        if (got < want) atomicSub(&C->inflight, want - got);
                     }
+                    if (got < want) atomicSub(&C->inflight, want - got);
                 }
             }
             got = __shfl_sync(kFull, got, 0);
             if (got == 0) continue;
+            gp = __shfl_sync(kFull, gp, 0);
+            p0 = __shfl_sync(kFull, p0, 0);
             base = __shfl_sync(kFull, base, 0);
+            const SlotDev *S = E.slots + s;
             int before = 0;
 #pragma unroll
             for (int t = 0; t < T; ++t) {
                 const unsigned m = idle[t];
                 const int rank = before + __popc(m & lt);
                 if (((m >> lane) & 1u) && rank < got) {
-                    init_lane(L[t], E, s, base + static_cast<unsigned long long>(rank), b);
+                    if (rank < gp)
+                        resume_lane(L[t], E, s, S->park[(p0 + static_cast<unsigned>(rank)) % S->park_cap]);
+                    else
+                        init_lane(L[t], E, s, base + static_cast<unsigned long long>(rank - gp));
                     ++n_active;
                 }
                 before += __popc(m);
@@ -257,38 +319,40 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
                                unsigned &n_cens) {
     const unsigned nb = E.chunk_blocks;
     while (b < nb) {
-        const float Jb = 4.0f * static_cast<float>(b);
-        float rr[T][2], tg[T][4];
+        float rr[T][2], tg[T][4], gs[T];
 #pragma unroll
         for (int t = 0; t < T; ++t) {
             const uint4 x = philox4x32_10(make_uint4(L[t].c_lo, L[t].c_hi, L[t].gid_lo, L[t].gid_hi),
                                           L[t].k0, L[t].k1);
             bm_pair_f32(x.x, x.y, L[t].bmc, rr[t][0], tg[t][0], tg[t][1]);
             bm_pair_f32(x.z, x.w, L[t].bmc, rr[t][1], tg[t][2], tg[t][3]);
+            gs[t] = fmaf(L[t].nudt, L[t].Jf, L[t].gb);
         }
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
-            const float J = Jb + static_cast<float>(s + 1);
 #pragma unroll
             for (int t = 0; t < T; ++t) {
-                step_f32<M>(L[t].r, L[t].v, rr[t][s >> 1], tg[t][s], fmaf(L[t].nudt, J, L[t].gb),
-                            L[t].dt, L[t].A, L[t].amp);
-                if (L[t].r >= L[t].hb || L[t].r < -kPiF) phase_event(L[t], E, s);
+                step_f32<M>(L[t].r, L[t].v, rr[t][s >> 1], tg[t][s],
+                            fmaf(L[t].nudt, static_cast<float>(s + 1), gs[t]), L[t].dt, L[t].A,
+                            L[t].amp);
+                if (L[t].r >= L[t].hb) phase_event(L[t], E, s);
             }
         }
         useful += 4ull * static_cast<unsigned>(n_active);
         bool ev = false;
 #pragma unroll
         for (int t = 0; t < T; ++t) {
+            if (L[t].r < -kPiF) wrap_down(L[t], E);
             L[t].c_lo += 1u;
             L[t].c_hi += (L[t].c_lo == 0u) ? 1u : 0u;
+            L[t].Jf += 4.0f;
             L[t].budget -= 1u;
             ev |= (L[t].esc >= 0) || (L[t].budget == 0u);
         }
         ++b;
         if (__any_sync(kFull, ev)) {
             finish_lanes(L, E, useful, n_active, n_esc, n_cens);
-            refill(L, E, M, b, n_active, cursor);
+            refill(L, E, M, n_active, cursor);
             if (!__any_sync(kFull, n_active > 0)) break;
         }
     }
@@ -325,11 +389,9 @@ __global__ void __launch_bounds__(256) engine_chunk_kernel(EngineDev E) {
         L[t].c_hi = E.lanes.c_hi[i];
         L[t].gid_lo = E.lanes.gid_lo[i];
         L[t].gid_hi = E.lanes.gid_hi[i];
-        L[t].budget = E.lanes.budget[i];
         L[t].esc = -1;
         load_consts(L[t], S);
-        const unsigned long long c = (static_cast<unsigned long long>(L[t].c_hi) << 32) | L[t].c_lo;
-        L[t].gb = static_cast<float>(S->gamma0 + S->nudt_d * static_cast<double>(4ull * c));
+        set_progress(L[t], S);
         ++n_active;
     }
     int kind = E.warp_kind[warp];
@@ -337,14 +399,14 @@ __global__ void __launch_bounds__(256) engine_chunk_kernel(EngineDev E) {
     unsigned cursor = E.warp_cursor[warp];
     unsigned long long useful = 0;
     unsigned n_esc = 0, n_cens = 0;
-    if (kind >= 0) refill(L, E, kind, 0u, n_active, cursor);
+    if (kind >= 0) refill(L, E, kind, n_active, cursor);
     unsigned b = 0;
     while (b < E.chunk_blocks) {
         if (kind < 0) {
             const int first = static_cast<int>(warp & 1u);
             for (int q = 0; q < 2 && kind < 0; ++q) {
                 const int m = first ^ q;
-                refill(L, E, m, b, n_active, cursor);
+                refill(L, E, m, n_active, cursor);
                 if (__any_sync(kFull, n_active > 0)) kind = m;
             }
             if (kind < 0) break;
@@ -355,6 +417,43 @@ __global__ void __launch_bounds__(256) engine_chunk_kernel(EngineDev E) {
             b = run_blocks<kOver, T>(L, E, b, n_active, cursor, useful, n_esc, n_cens);
         if (!__any_sync(kFull, n_active > 0)) kind = -1;
     }
+    // Preemption: a whole warp of this model may be asked to vacate (so it can switch model),
+    // or single lanes of requests above their share to suspend.  Suspended state goes to the
+    // request's ring; a push needs a free ring entry (park_used < park_cap).
+    bool vacate = false;
+    if (kind >= 0 && __any_sync(kFull, n_active > 0)) {
+        int v = 0;
+        if (lane == 0 && vload(E.vacate[kind]) > 0) v = atomicSub(&E.vacate[kind], 1) > 0 ? 1 : 0;
+        vacate = __shfl_sync(kFull, v, 0) != 0;
+    }
+#pragma unroll
+    for (int t = 0; t < T; ++t) {
+        const int s = L[t].slot;
+        if (s < 0) continue;
+        bool park = vacate;
+        if (!park && vload(E.preempt[s]) > 0) park = atomicSub(&E.preempt[s], 1) > 0;
+        if (!park) continue;
+        SlotCtl *C = E.ctl + s;
+        const SlotDev *S = E.slots + s;
+        if (atomicAdd(&C->park_used, 1) >= static_cast<int>(S->park_cap)) {
+            atomicSub(&C->park_used, 1);
+            continue;
+        }
+        const unsigned pi = atomicAdd(&C->park_tail, 1u);
+        ParkEntry &P = S->park[pi % S->park_cap];
+        P.r = L[t].r;
+        P.v = L[t].v;
+        P.w = L[t].w;
+        P.c_lo = L[t].c_lo;
+        P.c_hi = L[t].c_hi;
+        P.gid_lo = L[t].gid_lo;
+        P.gid_hi = L[t].gid_hi;
+        P.pad = 0;
+        atomicSub(&C->inflight, 1);
+        L[t].slot = -1;
+        --n_active;
+    }
+    if (!__any_sync(kFull, n_active > 0)) kind = -1;
 #pragma unroll
     for (int t = 0; t < T; ++t) {
         const unsigned i = t * nthreads + gtid;
@@ -368,7 +467,6 @@ __global__ void __launch_bounds__(256) engine_chunk_kernel(EngineDev E) {
         E.lanes.c_hi[i] = L[t].c_hi;
         E.lanes.gid_lo[i] = L[t].gid_lo;
         E.lanes.gid_hi[i] = L[t].gid_hi;
-        E.lanes.budget[i] = L[t].budget;
     }
     if (lane == 0) {
         E.warp_kind[warp] = kind;
@@ -400,6 +498,9 @@ __global__ void engine_scan_kernel(EngineDev E) {
     SlotCtl *C = E.ctl + s;
     if (C->state != kSlotActive) return;
     const SlotDev *S = E.slots + s;
+    // entries suspended during the launch become available to the next launch's refills
+    C->park_avail += static_cast<int>(C->park_tail - C->park_commit);
+    C->park_commit = C->park_tail;
     unsigned p = C->prefix;
     bool finished = false;
     while (p < S->n_idblocks) {

@@ -54,18 +54,17 @@ __device__ __forceinline__ void add128(unsigned long long &lo, unsigned long lon
 
 // Single-precision lane state (same step as the engine and the plain FP32 kernel).
 struct NLane {
-    float r, v, hb, gb;
+    float r, v, hb, gb, Jf;      // Jf = 4 x blocks since the bias base gb was set
     int w, esc;
     bool active;
     unsigned long long idx, c;   // trajectory index within the request, completed blocks
-    unsigned jb;                 // blocks since the bias base gb was set
 };
 
 __device__ __forceinline__ void nl_start(NLane &L, const NoAllocArgs &a, unsigned long long idx) {
     L.active = true;
     L.idx = idx;
     L.c = 0;
-    L.jb = 0;
+    L.Jf = 0.0f;
     L.r = a.r0;
     L.v = a.v0;
     L.w = a.w0;
@@ -108,10 +107,9 @@ __global__ void __launch_bounds__(kBlock) noalloc_kernel(NoAllocArgs a) {
     L.active = false;
     L.esc = -1;
     L.r = __int_as_float(0x7FFFFFFF);
-    L.v = L.hb = L.gb = 0.0f;
+    L.v = L.hb = L.gb = L.Jf = 0.0f;
     L.w = 0;
     L.idx = L.c = 0;
-    L.jb = 0;
     bool exhausted = false;
     nl_claim(L, a, head, exhausted);
     unsigned long long done = 0, esc = 0, s1lo = 0, s1hi = 0, s2lo = 0, s2hi = 0, under = 0, over = 0;
@@ -125,34 +123,34 @@ __global__ void __launch_bounds__(kBlock) noalloc_kernel(NoAllocArgs a) {
         float rr[2], tg[4];
         bm_pair_f32(x.x, x.y, a.bmc, rr[0], tg[0], tg[1]);
         bm_pair_f32(x.z, x.w, a.bmc, rr[1], tg[2], tg[3]);
-        const float Jb = 4.0f * static_cast<float>(L.jb);
+        const float gs = fmaf(a.nudt, L.Jf, L.gb);
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
-            step_f32<M>(L.r, L.v, rr[s >> 1], tg[s], fmaf(a.nudt, Jb + static_cast<float>(s + 1), L.gb),
+            step_f32<M>(L.r, L.v, rr[s >> 1], tg[s], fmaf(a.nudt, static_cast<float>(s + 1), gs),
                         a.dt, a.A, a.amp);
-            if (L.r >= L.hb || L.r < -kPiF) {
+            if (L.r >= L.hb) {
                 const float eb = fmaf(-kTwoPiF, static_cast<float>(L.w - a.w0), a.eb0);
                 if (L.r >= eb) {
                     if (L.esc < 0) L.esc = s;
                     L.r = __int_as_float(0x7FFFFFFF);
                 } else {
-                    if (L.r >= kPiF) {
-                        L.r -= kTwoPiF;
-                        L.w += 1;
-                    } else {
-                        L.r += kTwoPiF;
-                        L.w -= 1;
-                    }
+                    L.r -= kTwoPiF;
+                    L.w += 1;
                     L.hb = fminf(fmaf(-kTwoPiF, static_cast<float>(L.w - a.w0), a.eb0), kPiF);
                 }
             }
         }
+        if (L.r < -kPiF) {   // lower wrap at the block end
+            L.r += kTwoPiF;
+            L.w -= 1;
+            L.hb = fminf(fmaf(-kTwoPiF, static_cast<float>(L.w - a.w0), a.eb0), kPiF);
+        }
         if (L.active) {
             L.c += 1;
-            L.jb += 1;
-            if (L.jb == (1u << 20)) {   // re-base the single-precision bias
+            L.Jf += 4.0f;
+            if ((L.c & ((1ull << 20) - 1)) == 0) {   // re-base the single-precision bias
                 L.gb = static_cast<float>(a.gamma0 + a.nudt_d * static_cast<double>(4ull * L.c));
-                L.jb = 0;
+                L.Jf = 0.0f;
             }
             const bool out = L.c >= a.nblocks;
             if (L.esc >= 0 || out) {

@@ -63,7 +63,7 @@ done:
 
 // FP32: wrapped phase r in [-pi, pi) with winding w; escape when r >= eb = phi* - 2 pi w, the
 // threshold in the current cell's coordinates; hb = min(eb, pi) is the one bound tested every
-// step besides the lower wrap at -pi.
+// step; the lower wrap at -pi is applied at block ends.
 template <int M>
 __global__ void __launch_bounds__(256) plain_f32_kernel(PlainArgs a) {
     const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -76,21 +76,23 @@ __global__ void __launch_bounds__(256) plain_f32_kernel(PlainArgs a) {
     int64_t result = -1;
     uint64_t blk = 0;
     while (blk < nblocks) {
-        // re-base the single-precision bias every 2^20 blocks: gamma_k = gb + nudt * J
+        // re-base the single-precision bias every 2^20 blocks of the trajectory:
+        // gamma_k = (gb + nudt Jf) + nudt (s + 1), Jf = 4 x blocks since the base
         const uint64_t seg_end = blk + (1ull << 20) < nblocks ? blk + (1ull << 20) : nblocks;
         const float gb = static_cast<float>(a.gamma0 + a.nudt * static_cast<double>(4 * blk));
-        float J = 0.0f;
+        float Jf = 0.0f;
         for (; blk < seg_end; ++blk) {
             const uint4 x = philox4x32_10(make_uint4(lo32(blk), hi32(blk), lo32(gid), hi32(gid)),
                                           a.key0, a.key1);
             float rr[2], tg[4];
             bm_pair_f32(x.x, x.y, a.bmc_f, rr[0], tg[0], tg[1]);
             bm_pair_f32(x.z, x.w, a.bmc_f, rr[1], tg[2], tg[3]);
+            const float gs = fmaf(a.nudt_f, Jf, gb);
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
-                J += 1.0f;
-                step_f32<M>(r, v, rr[s >> 1], tg[s], fmaf(a.nudt_f, J, gb), a.dt_f, a.A_f, a.amp_f);
-                if (r >= hb || r < -kPiF) {
+                step_f32<M>(r, v, rr[s >> 1], tg[s], fmaf(a.nudt_f, static_cast<float>(s + 1), gs),
+                            a.dt_f, a.A_f, a.amp_f);
+                if (r >= hb) {
                     // threshold in the current cell: eb = phi* - 2 pi w (same rounding as the engine)
                     const float eb = fmaf(-kTwoPiF, static_cast<float>(w - a.w0), a.eb0_f);
                     if (r >= eb) {
@@ -98,16 +100,17 @@ __global__ void __launch_bounds__(256) plain_f32_kernel(PlainArgs a) {
                         if (k <= a.max_steps) result = static_cast<int64_t>(k);
                         goto done;
                     }
-                    if (r >= kPiF) {
-                        r -= kTwoPiF;
-                        w += 1;
-                    } else {
-                        r += kTwoPiF;
-                        w -= 1;
-                    }
+                    r -= kTwoPiF;
+                    w += 1;
                     hb = fminf(fmaf(-kTwoPiF, static_cast<float>(w - a.w0), a.eb0_f), kPiF);
                 }
             }
+            if (r < -kPiF) {   // lower wrap at the block end, as in the engine
+                r += kTwoPiF;
+                w -= 1;
+                hb = fminf(fmaf(-kTwoPiF, static_cast<float>(w - a.w0), a.eb0_f), kPiF);
+            }
+            Jf += 4.0f;
         }
     }
 done:

@@ -1,0 +1,56 @@
+"""Serving driver: Poisson arrivals of FPT requests into an engine that runs its own service
+thread (continuous batching: requests are admitted as slots and memory free up, and share the
+resident kernel with everything already on the device).
+
+Latency of a request = submission -> the service thread observing its completion (measured by
+the engine, fpt_result.latency_s).
+"""
+from __future__ import annotations
+
+import time
+
+import numpy as np
+
+from . import _lib
+
+
+def run_stream(stream, device: int = 0, chunk_steps: int = 4096, timeout_s: float = 600.0,
+               engine_kw=None):
+    """Submit (arrival_time_s, params dict) pairs at their arrival times and wait for all.
+    Returns a dict with latency percentiles and throughput."""
+    kw = dict(engine_kw or {})
+    kw.setdefault("chunk_steps", chunk_steps)
+    eng = _lib.Engine(device, service_thread=1, **kw)
+    try:
+        t0 = time.perf_counter()
+        ids = []
+        for t_arr, d in stream:
+            now = time.perf_counter() - t0
+            if t_arr > now:
+                time.sleep(t_arr - now)
+            ids.append(eng.submit(_lib.params_from(d), int(d["n_traj"]), int(d["seed"])))
+        t_submitted = time.perf_counter() - t0
+        lat, res = [], []
+        deadline = time.perf_counter() + timeout_s
+        for rid in ids:
+            left = max(deadline - time.perf_counter(), 0.001)
+            try:
+                r = eng.wait(rid, left)
+            except _lib.FptError:
+                r = None
+            res.append(r)
+            if r is not None:
+                lat.append(r.latency_s)
+        wall = time.perf_counter() - t0
+        c = eng.counters()
+    finally:
+        eng.close()
+    lat = np.array(lat) if lat else np.array([float("nan")])
+    return {
+        "requests": len(ids), "completed": int(sum(r is not None for r in res)),
+        "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+        "mean_s": float(np.mean(lat)), "wall_s": wall, "submit_span_s": t_submitted,
+        "steps_per_s": c["useful_steps"] / wall, "escapes_per_s": c["escapes"] / wall,
+        "trajectories_used": int(sum(r.n_used for r in res if r is not None)),
+        "chunk_steps": c["chunk_steps"],
+    }
