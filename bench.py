@@ -55,6 +55,8 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-requests", type=int, default=100)
     return ap.parse_args()
 
 
@@ -209,6 +211,13 @@ def run_reference(args):
 # our arm
 # ------------------------------------------------------------------------------------------
 
+# dram__bytes_read.sum + dram__bytes_write.sum of one resident-kernel launch of the current kernel
+# (ncu capture summarised in profiles/engine_chunk_kernel__overdamped_sweep.md): the lane state is
+# read and written once per launch, whatever the number of steps, so a 65 536-step launch moves
+# the same bytes as the captured 4096-step one.
+TRAFFIC_BYTES_PER_LAUNCH = 5.71e6
+
+
 def roofline_model(n_sm: int, f_mhz: float):
     """Peak trajectory-steps/s of the single-precision step from unit counts and clock.
 
@@ -278,6 +287,10 @@ def run_ours(args):
     barrier()
     torch.cuda.synchronize()
     c1 = eng.counters()
+    # accuracy of the FP32 engine on the gamma = 0.9, D = 0.2 point (finished in the timed run)
+    st_fast, res_fast = eng.poll(rids[11])
+    fast_point = ({"mean_fpt": res_fast.mean, "sem": res_fast.sem, "n": res_fast.n_used}
+                  if st_fast == 0 else None)
     ms = sum(a.elapsed_time(b) for a, b in evs)
     steps = c1["useful_steps"] - c0["useful_steps"]
     escapes = c1["escapes"] - c0["escapes"]
@@ -342,6 +355,7 @@ def run_ours(args):
         ms64 = a.elapsed_time(b)
         res, _, _ = api.reduce(d, st)
         fp64 = {"value": (res.steps_total) / (ms64 / 1e3), "unit": UNIT,
+                "fp32_engine_speedup": None,
                 "escapes_per_s": res.n_escaped / (ms64 / 1e3),
                 "sample": f"gamma=0.9 D=0.2 point, {n64} trajectories, one per thread, FP64",
                 "mean_fpt": res.mean, "sem": res.sem}
@@ -354,6 +368,18 @@ def run_ours(args):
         ms32 = a.elapsed_time(b)
         res32, _, _ = api.reduce(d32, st)
         fp64["fp32_plain_value"] = res32.steps_total / (ms32 / 1e3)
+
+    serving = None
+    if not args.no_serving and rank == 0 and world == 1:
+        from paper_1802_05065_gb300 import serving as _srv
+        sv = _srv.run_stream(workloads.serving_stream(n_requests=args.serving_requests),
+                             device=local, chunk_steps=4096, timeout_s=240.0)
+        serving = {"p50_latency_s": sv["p50_s"], "p99_latency_s": sv["p99_s"],
+                   "mean_latency_s": sv["mean_s"], "requests": sv["requests"],
+                   "completed": sv["completed"], "wall_s": sv["wall_s"],
+                   "steps_per_s": sv["steps_per_s"], "escapes_per_s": sv["escapes_per_s"],
+                   "stream": f"{args.serving_requests} requests, Poisson 200/s, uneven-batch "
+                             "parameters, 2^12..2^20 trajectories, 1 % RSE stop rule"}
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
@@ -376,11 +402,14 @@ def run_ours(args):
     kern_steps_s = steps / (kernel_ms / 1e3) if kernel_ms > 0 else None
     roof = {"bound": "alu", "achieved": kern_steps_s / 1e9 if kern_steps_s else None,
             "peak": peak / 1e9, "unit": "Gstep/s",
-            "frac": (kern_steps_s / peak) if kern_steps_s else None, "traffic": None,
+            "frac": (kern_steps_s / peak) if kern_steps_s else None,
+            "traffic": TRAFFIC_BYTES_PER_LAUNCH, "traffic_unit": "bytes per launch (lane state)",
             "pipe": "xu", "xu_ops_per_step": xu_step, "xu_ops_per_clk_per_sm": xu_rate,
             "sm_count": n_sm, "clock_mhz": f_max,
             "note": "achieved = useful steps / summed resident-kernel event time; peak = "
                     "16 XU ops/clk/SM x N_SM x max SM clock / 3 XU ops per step"}
+    if fp64:
+        fp64["fp32_engine_speedup"] = per_gpu_steps_s / fp64["value"]
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / max(args.steps, 1),
@@ -400,6 +429,8 @@ def run_ours(args):
         "cpu_baseline": cpu,
         "e2e": e2e,
         "fp64_plain": fp64,
+        "fp32_engine_point": fast_point,
+        "serving": serving,
         "gpu_launches": 2 * args.steps,
         "clocks": clocks,
     }

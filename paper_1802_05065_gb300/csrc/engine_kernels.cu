@@ -38,6 +38,7 @@ struct Lane {
     float gb, Jf;         // bias base and 4 x blocks since the base (exact)
     float dt, A, amp, bmc, nudt;
     unsigned k0, k1;
+    PhiloxKeys K;         // round keys of the request's seed
 };
 
 __device__ __forceinline__ float qnan_f() { return __int_as_float(0x7FFFFFFF); }
@@ -70,6 +71,7 @@ __device__ __forceinline__ void load_consts(Lane &L, const SlotDev *S) {
     L.nudt = S->nudt;
     L.k0 = S->key0;
     L.k1 = S->key1;
+    philox_keys(L.K, L.k0, L.k1);
 }
 
 __device__ __forceinline__ unsigned long long lane_c(const Lane &L) {
@@ -322,11 +324,22 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
         float rr[T][2], tg[T][4], gs[T];
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-            const uint4 x = philox4x32_10(make_uint4(L[t].c_lo, L[t].c_hi, L[t].gid_lo, L[t].gid_hi),
-                                          L[t].k0, L[t].k1);
+            const uint4 x = philox4x32_10k(make_uint4(L[t].c_lo, L[t].c_hi, L[t].gid_lo, L[t].gid_hi),
+                                           L[t].K);
             bm_pair_f32(x.x, x.y, L[t].bmc, rr[t][0], tg[t][0], tg[t][1]);
             bm_pair_f32(x.z, x.w, L[t].bmc, rr[t][1], tg[t][2], tg[t][3]);
             gs[t] = fmaf(L[t].nudt, L[t].Jf, L[t].gb);
+        }
+        // Four steps without a branch: each lane only tracks the largest phase of the block.
+        // In the rare block where it reached the lane's bound hb, that lane's block is replayed
+        // from the saved start state with the event test after every step, so wraps and the
+        // escape step are exactly those of a step-by-step test.
+        float r0s[T], v0s[T], mx[T];
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            r0s[t] = L[t].r;
+            v0s[t] = L[t].v;
+            mx[t] = -INFINITY;
         }
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
@@ -335,7 +348,21 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
                 step_f32<M>(L[t].r, L[t].v, rr[t][s >> 1], tg[t][s],
                             fmaf(L[t].nudt, static_cast<float>(s + 1), gs[t]), L[t].dt, L[t].A,
                             L[t].amp);
-                if (L[t].r >= L[t].hb) phase_event(L[t], E, s);
+                mx[t] = fmaxf(mx[t], L[t].r);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < T; ++t) {
+            if (mx[t] >= L[t].hb) {
+                L[t].r = r0s[t];
+                L[t].v = v0s[t];
+#pragma unroll
+                for (int s = 0; s < 4; ++s) {
+                    step_f32<M>(L[t].r, L[t].v, rr[t][s >> 1], tg[t][s],
+                                fmaf(L[t].nudt, static_cast<float>(s + 1), gs[t]), L[t].dt,
+                                L[t].A, L[t].amp);
+                    if (L[t].r >= L[t].hb) phase_event(L[t], E, s);
+                }
             }
         }
         useful += 4ull * static_cast<unsigned>(n_active);

@@ -23,6 +23,32 @@ constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
 constexpr float kPiF = 3.14159265358979323846f;
 constexpr float kTwoPiF = 6.28318530717958647692f;
 
+// Round keys of Philox4x32-10 for one key: k_r = k + r W (mod 2^32), r = 0..9.  A lane that
+// keeps them in registers spends no instruction on the key schedule per call.
+struct PhiloxKeys {
+    uint32_t a[10], b[10];
+};
+
+__device__ __forceinline__ void philox_keys(PhiloxKeys &K, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        K.a[r] = k0 + static_cast<uint32_t>(r) * kPhiloxW0;
+        K.b[r] = k1 + static_cast<uint32_t>(r) * kPhiloxW1;
+    }
+}
+
+// Philox4x32-10 with precomputed round keys (same output as philox4x32_10 below).
+__device__ __forceinline__ uint4 philox4x32_10k(uint4 c, const PhiloxKeys &K) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        const uint64_t p0 = static_cast<uint64_t>(kPhiloxM0) * c.x;
+        const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * c.z;
+        c = make_uint4(static_cast<uint32_t>(p1 >> 32) ^ c.y ^ K.a[round], static_cast<uint32_t>(p1),
+                       static_cast<uint32_t>(p0 >> 32) ^ c.w ^ K.b[round], static_cast<uint32_t>(p0));
+    }
+    return c;
+}
+
 // Philox4x32-10: ten rounds of two 32x32->64 multiplies; the key advances by the Weyl
 // constants between rounds.
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {

@@ -7,7 +7,7 @@
 
 #include <cuda_runtime.h>
 
-#include "../../include/fpt.h"
+#include "fpt.h"
 
 namespace fpt {
 
