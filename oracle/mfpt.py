@@ -71,6 +71,42 @@ def overdamped_mfpt_double(gamma: float, D: float, A: float = 1.0, x0: float | N
     return (1.0 / D) * integral / (-math.expm1(-2.0 * math.pi * gamma / D))
 
 
+def overdamped_mfpt_to(gamma: float, D: float, b: float, A: float = 1.0, x0: float | None = None,
+                       panels: int = 128) -> float:
+    """Mean time from x0 to an arbitrary level b > x0 (same double integral, outer limits
+    [x0, b])."""
+    if x0 is None:
+        x0 = math.asin(gamma / A)
+
+    def U(z):
+        return -A * np.cos(z) - gamma * z
+
+    xs, wx = _gl_panels(x0, b, panels)
+    ss, ws = _gl_panels(0.0, 2.0 * math.pi, panels)
+    X = xs[:, None]
+    inner = np.exp((U(X) - U(X - ss[None, :])) / D) @ ws
+    return (1.0 / D) * float(np.dot(wx, inner)) / (-math.expm1(-2.0 * math.pi * gamma / D))
+
+
+def threshold_sensitivity(gamma: float, D: float, A: float = 1.0, panels: int = 2048) -> float:
+    """dT/db at the level b = x0 + 2 pi: the outer integrand of the MFPT formula at b, which by
+    periodicity equals its value at x0."""
+    x0 = math.asin(gamma / A)
+    s, w = _gl_panels(0.0, 2.0 * math.pi, panels)
+    inner = float(np.sum(w * np.exp((-A * math.cos(x0) + A * np.cos(x0 - s) - gamma * s) / D)))
+    return inner / D / (-math.expm1(-2.0 * math.pi * gamma / D))
+
+
+def monitoring_shift(gamma: float, D: float, dt: float, A: float = 1.0) -> float:
+    """Delay of the detected first passage when the level is tested once per step (as in
+    Alg. 1): the continuity correction of Broadie, Glasserman and Kou moves the level up by
+    beta sigma_step, beta = -zeta(1/2)/sqrt(2 pi) = 0.5826, sigma_step = sqrt(2 D dt); to first
+    order the mean passage time grows by beta sigma_step dT/db."""
+    from scipy.special import zeta
+    beta = -float(zeta(0.5)) / math.sqrt(2.0 * math.pi)
+    return beta * math.sqrt(2.0 * D * dt) * threshold_sensitivity(gamma, D, A)
+
+
 def overdamped_mfpt(gamma: float, D: float, A: float = 1.0, rtol: float = 1e-12) -> float:
     """Exact overdamped MFPT over one period, converged by doubling the panel count."""
     panels = 64

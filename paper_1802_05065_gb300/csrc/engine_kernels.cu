@@ -80,7 +80,8 @@ __device__ __forceinline__ unsigned long long lane_c(const Lane &L) {
 
 // Bias base and event countdown from the trajectory's block count c:
 // gb = gamma0 + nu dt 4 c_base (FP64, rounded once), Jf = 4 (c - c_base),
-// budget = blocks until the step budget ends or the next re-base, whichever is first.
+// budget = blocks until the step budget ends, the next re-base or the next carry of the low
+// 32-bit word of c, whichever is first (the high word is only updated at that event).
 __device__ __forceinline__ void set_progress(Lane &L, const SlotDev *S) {
     const unsigned long long c = lane_c(L);
     const unsigned long long cb = c - (c % kRebaseBlocks);
@@ -88,7 +89,10 @@ __device__ __forceinline__ void set_progress(Lane &L, const SlotDev *S) {
     L.Jf = static_cast<float>(4ull * (c - cb));
     const unsigned long long to_end = S->nblocks > c ? S->nblocks - c : 0ull;
     const unsigned long long to_base = kRebaseBlocks - (c - cb);
-    L.budget = static_cast<unsigned>(to_end < to_base ? to_end : to_base);
+    const unsigned long long to_carry = 0x100000000ull - (c & 0xFFFFFFFFull);
+    unsigned long long m = to_end < to_base ? to_end : to_base;
+    m = m < to_carry ? m : to_carry;
+    L.budget = static_cast<unsigned>(m);
 }
 
 // Start trajectory `idx` of request slot s.
@@ -331,9 +335,9 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
             gs[t] = fmaf(L[t].nudt, L[t].Jf, L[t].gb);
         }
         // Four steps without a branch: each lane only tracks the largest phase of the block.
-        // In the rare block where it reached the lane's bound hb, that lane's block is replayed
-        // from the saved start state with the event test after every step, so wraps and the
-        // escape step are exactly those of a step-by-step test.
+        // In the rare block where it reached the lane's bound hb, the lane's block is replayed
+        // (in the warp's event path below) from the saved start state with the event test after
+        // every step, so wraps and the escape step are exactly those of a step-by-step test.
         float r0s[T], v0s[T], mx[T];
 #pragma unroll
         for (int t = 0; t < T; ++t) {
@@ -351,33 +355,35 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
                 mx[t] = fmaxf(mx[t], L[t].r);
             }
         }
-#pragma unroll
-        for (int t = 0; t < T; ++t) {
-            if (mx[t] >= L[t].hb) {
-                L[t].r = r0s[t];
-                L[t].v = v0s[t];
-#pragma unroll
-                for (int s = 0; s < 4; ++s) {
-                    step_f32<M>(L[t].r, L[t].v, rr[t][s >> 1], tg[t][s],
-                                fmaf(L[t].nudt, static_cast<float>(s + 1), gs[t]), L[t].dt,
-                                L[t].A, L[t].amp);
-                    if (L[t].r >= L[t].hb) phase_event(L[t], E, s);
-                }
-            }
-        }
         useful += 4ull * static_cast<unsigned>(n_active);
         bool ev = false;
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-            if (L[t].r < -kPiF) wrap_down(L[t], E);
             L[t].c_lo += 1u;
-            L[t].c_hi += (L[t].c_lo == 0u) ? 1u : 0u;
             L[t].Jf += 4.0f;
             L[t].budget -= 1u;
-            ev |= (L[t].esc >= 0) || (L[t].budget == 0u);
+            // one vote covers every rare case: a bound reached (escape or upper wrap), the
+            // countdown (step budget, bias re-base, low-word carry) and the lower wrap
+            ev |= (mx[t] >= L[t].hb) || (L[t].budget == 0u) || (L[t].r < -kPiF);
         }
         ++b;
         if (__any_sync(kFull, ev)) {
+#pragma unroll
+            for (int t = 0; t < T; ++t) {
+                if (mx[t] >= L[t].hb) {
+                    L[t].r = r0s[t];
+                    L[t].v = v0s[t];
+#pragma unroll
+                    for (int s = 0; s < 4; ++s) {
+                        step_f32<M>(L[t].r, L[t].v, rr[t][s >> 1], tg[t][s],
+                                    fmaf(L[t].nudt, static_cast<float>(s + 1), gs[t]), L[t].dt,
+                                    L[t].A, L[t].amp);
+                        if (L[t].r >= L[t].hb) phase_event(L[t], E, s);
+                    }
+                }
+                if (L[t].r < -kPiF) wrap_down(L[t], E);
+                if (L[t].slot >= 0 && L[t].c_lo == 0u) L[t].c_hi += 1u;   // 2^32-block carry
+            }
             finish_lanes(L, E, useful, n_active, n_esc, n_cens);
             refill(L, E, M, n_active, cursor);
             if (!__any_sync(kFull, n_active > 0)) break;

@@ -79,3 +79,21 @@ def test_paper_fig7_barrier():
         gold = json.load(f)
     val = gold["V0"] * mfpt.barrier(gold["gamma"])
     assert round(val, 4) == gold["delta_U"]
+
+
+@pytest.mark.parametrize("g,D", [(0.9, 0.2), (0.7, 0.1), (0.5, 0.2)])
+def test_threshold_sensitivity_by_finite_difference(g, D):
+    """dT/db from the integrand equals the finite difference of the double integral taken to
+    levels b +- h around x0 + 2 pi; the full-period endpoint also reproduces T."""
+    x0 = math.asin(g)
+    b = x0 + 2 * math.pi
+    h = 1e-3
+    fd = (mfpt.overdamped_mfpt_to(g, D, b + h) - mfpt.overdamped_mfpt_to(g, D, b - h)) / (2 * h)
+    assert math.isclose(mfpt.threshold_sensitivity(g, D), fd, rel_tol=1e-5)
+    assert math.isclose(mfpt.overdamped_mfpt_to(g, D, b), mfpt.overdamped_mfpt(g, D), rel_tol=1e-9)
+
+
+def test_monitoring_constant():
+    """beta = -zeta(1/2)/sqrt(2 pi) = 0.5826 (Broadie-Glasserman-Kou)."""
+    assert abs(mfpt.monitoring_shift(0.9, 0.2, 1e-3) /
+               (math.sqrt(2 * 0.2 * 1e-3) * mfpt.threshold_sensitivity(0.9, 0.2)) - 0.5826) < 1e-4
