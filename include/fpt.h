@@ -191,6 +191,19 @@ fpt_status fpt_per_traj(fpt_engine *e, uint64_t req_id, double *out, uint64_t n)
 /* Same as escape steps (host, n int64; -1 censored). */
 fpt_status fpt_per_traj_steps(fpt_engine *e, uint64_t req_id, int64_t *out, uint64_t n);
 
+/* Checkpoint a running (or queued) request: its lanes are suspended into its ring at the end of
+ * the next launch, then its whole state -- parameters, queue head, exact sums, id-block
+ * accumulators, histogram rows, per-trajectory steps and suspended trajectories -- is written
+ * to the host buffer `buf`, and the request is released.  With buf == NULL only *size is set
+ * (an upper bound); otherwise *size is the buffer's capacity on input and the bytes written on
+ * output.  fpt_restore continues it exactly: every trajectory ends with the escape step it
+ * would have had without the interruption (the paper's 2-day runs, Sec. IV.B, motivate it).
+ * Drives the engine itself when there is no service thread. */
+fpt_status fpt_checkpoint(fpt_engine *e, uint64_t req_id, void *buf, size_t *size);
+
+/* Re-admit a request from a checkpoint (host buffer of `size` bytes); *req_id gets its new id. */
+fpt_status fpt_restore(fpt_engine *e, const void *buf, size_t size, uint64_t *req_id);
+
 /* Free a finished (or cancel a running) request and its device memory. */
 fpt_status fpt_release(fpt_engine *e, uint64_t req_id);
 

@@ -89,7 +89,7 @@ EXPORTS = [
     "fpt_step", "fpt_poll", "fpt_wait", "fpt_histogram", "fpt_per_traj", "fpt_per_traj_steps",
     "fpt_release", "fpt_get_counters", "fpt_engine_stream", "fpt_destroy", "fpt_last_error",
     "fpt_status_string", "fpt_philox_fill", "fpt_normals_fill", "fpt_version",
-    "fpt_request_sums", "fpt_run_noalloc",
+    "fpt_request_sums", "fpt_run_noalloc", "fpt_checkpoint", "fpt_restore",
 ]
 
 _lib = None
@@ -118,6 +118,8 @@ def load() -> ctypes.CDLL:
     L.fpt_per_traj.argtypes = [vp, u64, P(f64), u64]
     L.fpt_request_sums.argtypes = [vp, u64, P(Sums)]
     L.fpt_run_noalloc.argtypes = [P(Params), u64, u64, vp, vp, vp, vp]
+    L.fpt_checkpoint.argtypes = [vp, u64, vp, P(ctypes.c_size_t)]
+    L.fpt_restore.argtypes = [vp, vp, ctypes.c_size_t, P(u64)]
     L.fpt_per_traj_steps.argtypes = [vp, u64, P(ctypes.c_int64), u64]
     L.fpt_release.argtypes = [vp, u64]
     L.fpt_get_counters.argtypes = [vp, P(EngineCounters)]
@@ -135,7 +137,7 @@ def load() -> ctypes.CDLL:
                  "fpt_submit", "fpt_step", "fpt_poll", "fpt_wait", "fpt_histogram",
                  "fpt_per_traj", "fpt_per_traj_steps", "fpt_release", "fpt_get_counters",
                  "fpt_destroy", "fpt_philox_fill", "fpt_normals_fill", "fpt_request_sums",
-                 "fpt_run_noalloc"):
+                 "fpt_run_noalloc", "fpt_checkpoint", "fpt_restore"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -280,6 +282,19 @@ class Engine:
         s = Sums()
         _check(self._L.fpt_request_sums(self._h, rid, ctypes.byref(s)), self._h)
         return s
+
+    def checkpoint(self, rid: int) -> bytes:
+        """Suspend and serialise a request (then released); see fpt_checkpoint."""
+        n = ctypes.c_size_t(0)
+        _check(self._L.fpt_checkpoint(self._h, rid, None, ctypes.byref(n)), self._h)
+        buf = ctypes.create_string_buffer(n.value)
+        _check(self._L.fpt_checkpoint(self._h, rid, buf, ctypes.byref(n)), self._h)
+        return buf.raw[: n.value]
+
+    def restore(self, blob: bytes) -> int:
+        rid = ctypes.c_uint64()
+        _check(self._L.fpt_restore(self._h, blob, len(blob), ctypes.byref(rid)), self._h)
+        return rid.value
 
     def release(self, rid: int):
         _check(self._L.fpt_release(self._h, rid), self._h)

@@ -58,7 +58,22 @@ struct Request {
     fpt_sums sums{};
     fpt_result result{};
     Clock::time_point t_submit;
+    bool suspending = false;          // checkpoint requested: no new work, lanes park
+    bool quiesced = false;            // no lane holds a trajectory; all suspended ones committed
+    std::vector<uint8_t> restore;     // checkpoint payload to load at admission
 };
+
+// Serialised request (fpt_checkpoint / fpt_restore): header, then SlotCtl, id-block accumulators,
+// histogram rows, per-trajectory steps (if kept) and suspended trajectories.
+struct CkptHeader {
+    uint64_t magic, version;
+    fpt_params params;
+    uint64_t n_traj, seed;
+    uint32_t stop_block, n_idblocks;
+    uint64_t n_park, has_per_traj;
+};
+constexpr uint64_t kCkptMagic = 0x5450464B43505446ull;   // "FTPCKFPT"
+constexpr uint64_t kCkptVersion = 1;
 
 // Ring of suspended trajectories: never more than the lanes can hold twice over.
 uint32_t park_capacity(uint64_t n_traj, unsigned lanes) {
@@ -232,6 +247,34 @@ fpt_status admit(fpt_engine *e) {
         CK(cudaMemcpyAsync(e->d_slots + s, &S, sizeof(SlotDev), cudaMemcpyHostToDevice, e->stream));
         SlotCtl &C = e->h_ctl_init[s];
         std::memset(&C, 0, sizeof(C));
+        if (!R.restore.empty()) {
+            // continue a checkpointed request: counters, accumulators, histogram rows,
+            // per-trajectory steps and suspended trajectories (re-based to ring index 0)
+            const uint8_t *q = R.restore.data();
+            const CkptHeader &H = *reinterpret_cast<const CkptHeader *>(q);
+            q += sizeof(CkptHeader);
+            std::memcpy(&C, q, sizeof(SlotCtl));
+            q += sizeof(SlotCtl);
+            const size_t acc_b = nb * sizeof(IdBlockAcc), hist_b = nb * static_cast<size_t>(R.params.hist_bins) * 4;
+            CK(cudaMemcpyAsync(R.acc, q, acc_b, cudaMemcpyHostToDevice, e->stream));
+            q += acc_b;
+            CK(cudaMemcpyAsync(R.hist, q, hist_b, cudaMemcpyHostToDevice, e->stream));
+            q += hist_b;
+            if (H.has_per_traj) {
+                if (R.per_traj)
+                    CK(cudaMemcpyAsync(R.per_traj, q, R.n_traj * 8, cudaMemcpyHostToDevice, e->stream));
+                q += R.n_traj * 8;
+            }
+            const unsigned np = static_cast<unsigned>(H.n_park);
+            if (np) CK(cudaMemcpyAsync(R.park, q, np * sizeof(ParkEntry), cudaMemcpyHostToDevice, e->stream));
+            C.inflight = 0;
+            C.park_head = 0;
+            C.park_tail = C.park_commit = np;
+            C.park_avail = C.park_used = static_cast<int>(np);
+            CK(cudaStreamSynchronize(e->stream));   // the payload is host memory we free below
+            R.restore.clear();
+            R.restore.shrink_to_fit();
+        }
         C.state = kSlotActive;
         CK(cudaMemcpyAsync(e->d_ctl + s, &C, sizeof(SlotCtl), cudaMemcpyHostToDevice, e->stream));
         e->slot_req[s] = R.id;
@@ -256,6 +299,10 @@ void build_lists(fpt_engine *e) {
         if (!e->slot_req[s]) continue;
         Request &R = *e->reqs[e->slot_req[s]];
         if (R.phase != kRunning) continue;
+        if (R.suspending) {                 // checkpoint: no new work, every lane suspends
+            e->h_preempt[s] = 1 << 30;
+            continue;
+        }
         e->h_act[R.dec.model * e->maxr + cnt[R.dec.model]++] = s;
         ++active;
     }
@@ -265,13 +312,15 @@ void build_lists(fpt_engine *e) {
     const int cap = active ? share + 32 : 0;
     for (int s = 0; s < e->maxr; ++s) e->h_caps[s] = cap;
     e->h_flags[0] = e->h_flags[1] = e->h_flags[2] = 0;
+    for (int s = 0; s < e->maxr; ++s)
+        if (e->h_preempt[s]) e->h_flags[2] = 1;   // keep a suspending request's lanes from refilling
     if (active < 2) return;
     int64_t deficit[2] = {0, 0};
     bool over[2] = {false, false};
     for (int s = 0; s < e->maxr; ++s) {
         if (!e->slot_req[s]) continue;
         Request &R = *e->reqs[e->slot_req[s]];
-        if (R.phase != kRunning) continue;
+        if (R.phase != kRunning || R.suspending) continue;
         const SlotCtl &C = e->h_ctl[s];
         if (C.state != kSlotActive) continue;     // not yet launched or finishing
         const int64_t unclaimed = C.head < R.n_traj ? static_cast<int64_t>(R.n_traj - C.head) : 0;
@@ -285,7 +334,7 @@ void build_lists(fpt_engine *e) {
     for (int s = 0; s < e->maxr; ++s) {
         if (!e->slot_req[s]) continue;
         Request &R = *e->reqs[e->slot_req[s]];
-        if (R.phase != kRunning) continue;
+        if (R.phase != kRunning || R.suspending) continue;
         const SlotCtl &C = e->h_ctl[s];
         if (C.state != kSlotActive || C.inflight <= share) continue;
         const int room = static_cast<int>(R.park_cap) - std::max(C.park_used, 0);
@@ -351,6 +400,8 @@ void process_status(fpt_engine *e) {
             finalize(e, R, C);
             R.phase = kFinished;
         }
+        if (R.phase == kRunning && R.suspending && C.inflight == 0 && C.park_commit == C.park_tail)
+            R.quiesced = true;
         if ((R.phase == kFinished || R.phase == kCancelled) && C.state != kSlotActive &&
             C.inflight == 0) {
             e->slot_req[s] = 0;
@@ -608,8 +659,10 @@ extern "C" fpt_status fpt_create(const fpt_engine_config *config, fpt_engine **o
     return FPT_OK;
 }
 
-extern "C" fpt_status fpt_submit(fpt_engine *e, const fpt_params *params, uint64_t n_traj,
-                                 uint64_t seed, uint64_t *req_id) {
+// Validate and queue a request; `payload` (checkpoint bytes) is attached before it becomes
+// visible to the admission path.
+static fpt_status submit_impl(fpt_engine *e, const fpt_params *params, uint64_t n_traj,
+                              uint64_t seed, uint64_t *req_id, std::vector<uint8_t> *payload) {
     if (!e || !params || !req_id) return fail(e, FPT_EINVAL, "NULL argument");
     auto R = std::make_unique<Request>();
     std::string err;
@@ -626,6 +679,7 @@ extern "C" fpt_status fpt_submit(fpt_engine *e, const fpt_params *params, uint64
     R->n_idblocks = static_cast<uint32_t>(nb);
     if (request_bytes(*params, n_traj, R->stop_block, e->lanes) > e->budget)
         return fail(e, FPT_ENOMEM, "request larger than the engine's memory budget");
+    if (payload) R->restore.swap(*payload);
     R->t_submit = Clock::now();
     {
         std::lock_guard<std::mutex> lk(e->mu);
@@ -638,6 +692,11 @@ extern "C" fpt_status fpt_submit(fpt_engine *e, const fpt_params *params, uint64
     }
     e->cv_work.notify_all();
     return FPT_OK;
+}
+
+extern "C" fpt_status fpt_submit(fpt_engine *e, const fpt_params *params, uint64_t n_traj,
+                                 uint64_t seed, uint64_t *req_id) {
+    return submit_impl(e, params, n_traj, seed, req_id, nullptr);
 }
 
 extern "C" fpt_status fpt_step(fpt_engine *e, int n_iterations) {
@@ -779,6 +838,133 @@ extern "C" fpt_status fpt_per_traj(fpt_engine *e, uint64_t req_id, double *out, 
 extern "C" fpt_status fpt_per_traj_steps(fpt_engine *e, uint64_t req_id, int64_t *out, uint64_t n) {
     if (!e || (!out && n)) return fail(e, FPT_EINVAL, "NULL argument");
     return per_traj_impl(e, req_id, out, nullptr, n);
+}
+
+// Bytes of a checkpoint of R: header, control block, accumulators, histogram rows,
+// per-trajectory steps (if kept) and at most the ring's capacity of suspended trajectories.
+static size_t ckpt_bound(const Request &R, unsigned lanes) {
+    size_t b = sizeof(CkptHeader) + sizeof(SlotCtl) + R.n_idblocks * sizeof(IdBlockAcc) +
+               static_cast<size_t>(R.n_idblocks) * R.params.hist_bins * 4 +
+               static_cast<size_t>(park_capacity(R.n_traj, lanes)) * sizeof(ParkEntry);
+    if (R.params.keep_per_traj) b += R.n_traj * 8;
+    return b;
+}
+
+extern "C" fpt_status fpt_checkpoint(fpt_engine *e, uint64_t req_id, void *buf, size_t *size) {
+    if (!e || !size) return fail(e, FPT_EINVAL, "NULL argument");
+    {
+        std::lock_guard<std::mutex> lk(e->mu);
+        Request *R = find(e, req_id);
+        if (!R) return fail(e, FPT_ENOTFOUND, "unknown request id");
+        if (R->phase == kFinished || R->phase == kCancelled)
+            return fail(e, FPT_EINVAL, "request already finished or cancelled");
+        const size_t bound = ckpt_bound(*R, e->lanes);
+        if (!buf) {
+            *size = bound;
+            return FPT_OK;
+        }
+        if (*size < bound) return fail(e, FPT_EINVAL, "checkpoint buffer too small");
+        R->suspending = true;
+    }
+    e->cv_work.notify_all();
+    // wait until the request's lanes have suspended (drive the engine without a service thread)
+    for (int it = 0; it < 1000; ++it) {
+        {
+            std::unique_lock<std::mutex> lk(e->mu);
+            Request *R = find(e, req_id);
+            if (!R) return fail(e, FPT_ENOTFOUND, "request vanished");
+            if (R->quiesced || R->phase == kPending || R->phase == kFinished) break;
+            if (e->broken) return fail(e, FPT_ECUDA, "engine is in an error state: " + e->error);
+            if (e->cfg.service_thread) {
+                e->cv_done.wait_for(lk, std::chrono::milliseconds(100));
+                continue;
+            }
+        }
+        std::lock_guard<std::mutex> dk(e->drive_mu);
+        cudaSetDevice(e->device);
+        const fpt_status st = iteration(e);
+        if (st != FPT_OK) return st;
+    }
+    std::lock_guard<std::mutex> dk(e->drive_mu);   // no launch may run while we read
+    std::lock_guard<std::mutex> lk(e->mu);
+    Request *R = find(e, req_id);
+    if (!R) return fail(e, FPT_ENOTFOUND, "request vanished");
+    CK(cudaSetDevice(e->device));
+    uint8_t *q = static_cast<uint8_t *>(buf);
+    CkptHeader H{};
+    H.magic = kCkptMagic;
+    H.version = kCkptVersion;
+    H.params = R->params;
+    H.n_traj = R->n_traj;
+    H.seed = R->seed;
+    H.stop_block = R->stop_block;
+    H.n_idblocks = R->n_idblocks;
+    H.has_per_traj = R->params.keep_per_traj ? 1 : 0;
+    SlotCtl C{};
+    if (R->phase == kPending) {
+        H.n_park = 0;
+    } else if (!R->quiesced) {
+        return fail(e, FPT_ETIMEDOUT, "request did not quiesce");
+    } else {
+        CK(cudaMemcpy(&C, e->d_ctl + R->slot, sizeof(SlotCtl), cudaMemcpyDeviceToHost));
+        H.n_park = C.park_tail - C.park_head;
+    }
+    const size_t nb = R->n_idblocks, hist_b = nb * static_cast<size_t>(R->params.hist_bins) * 4;
+    std::memcpy(q, &H, sizeof(H));
+    q += sizeof(H);
+    std::memcpy(q, &C, sizeof(C));
+    q += sizeof(C);
+    if (R->phase == kPending) {
+        std::memset(q, 0, nb * sizeof(IdBlockAcc) + hist_b + (H.has_per_traj ? R->n_traj * 8 : 0));
+        q += nb * sizeof(IdBlockAcc) + hist_b;
+        if (H.has_per_traj) {
+            std::memset(q, 0xFF, R->n_traj * 8);
+            q += R->n_traj * 8;
+        }
+    } else {
+        CK(cudaMemcpy(q, R->acc, nb * sizeof(IdBlockAcc), cudaMemcpyDeviceToHost));
+        q += nb * sizeof(IdBlockAcc);
+        CK(cudaMemcpy(q, R->hist, hist_b, cudaMemcpyDeviceToHost));
+        q += hist_b;
+        if (H.has_per_traj) {
+            CK(cudaMemcpy(q, R->per_traj, R->n_traj * 8, cudaMemcpyDeviceToHost));
+            q += R->n_traj * 8;
+        }
+        for (unsigned i = 0; i < H.n_park; ++i) {
+            const unsigned idx = (C.park_head + i) % R->park_cap;
+            CK(cudaMemcpy(q, R->park + idx, sizeof(ParkEntry), cudaMemcpyDeviceToHost));
+            q += sizeof(ParkEntry);
+        }
+    }
+    *size = static_cast<size_t>(q - static_cast<uint8_t *>(buf));
+    // release: the slot is freed after the device state says no lane holds it
+    R->released = true;
+    if (R->phase == kPending) {
+        e->pending.erase(std::find(e->pending.begin(), e->pending.end(), req_id));
+        e->reqs.erase(req_id);
+    } else {
+        R->phase = kCancelled;
+        static const int cancelled = kSlotCancelled;
+        CK(cudaMemcpy(&e->d_ctl[R->slot].state, &cancelled, sizeof(int), cudaMemcpyHostToDevice));
+    }
+    return FPT_OK;
+}
+
+extern "C" fpt_status fpt_restore(fpt_engine *e, const void *buf, size_t size, uint64_t *req_id) {
+    if (!e || !buf || !req_id) return fail(e, FPT_EINVAL, "NULL argument");
+    if (size < sizeof(CkptHeader) + sizeof(SlotCtl)) return fail(e, FPT_EINVAL, "checkpoint too short");
+    CkptHeader H;
+    std::memcpy(&H, buf, sizeof(H));
+    if (H.magic != kCkptMagic || H.version != kCkptVersion) return fail(e, FPT_EINVAL, "not a checkpoint");
+    const size_t nb = H.n_idblocks;
+    const size_t want = sizeof(CkptHeader) + sizeof(SlotCtl) + nb * sizeof(IdBlockAcc) +
+                        nb * static_cast<size_t>(H.params.hist_bins) * 4 +
+                        (H.has_per_traj ? H.n_traj * 8 : 0) + H.n_park * sizeof(ParkEntry);
+    if (size != want) return fail(e, FPT_EINVAL, "checkpoint size does not match its header");
+    if (H.n_park > park_capacity(H.n_traj, e->lanes))
+        return fail(e, FPT_EINVAL, "checkpoint holds more suspended trajectories than this engine's ring");
+    std::vector<uint8_t> payload(static_cast<const uint8_t *>(buf), static_cast<const uint8_t *>(buf) + size);
+    return submit_impl(e, &H.params, H.n_traj, H.seed, req_id, &payload);
 }
 
 extern "C" fpt_status fpt_release(fpt_engine *e, uint64_t req_id) {

@@ -273,3 +273,47 @@ def test_suspended_trajectories_resume_exactly(lib, api, target):
     assert c["preempted"] > 0
     ref = api.run_plain(target, n, seed).cpu().numpy()
     assert (steps == ref).all()
+
+
+@pytest.mark.parametrize("target", [CONST_UNDER, RAMP], ids=["constant", "ramp"])
+@pytest.mark.parametrize("service", [0, 1])
+def test_checkpoint_restore_is_exact(lib, api, target, service):
+    """A request checkpointed mid-run (lanes suspended, state serialised, engine destroyed) and
+    restored into a differently shaped engine finishes with exactly the per-trajectory steps and
+    sums of an uninterrupted run."""
+    import time
+    n, seed = 2**20, 123          # more trajectories than lanes: some still unclaimed
+    with _engine(lib, chunk_steps=2048, service_thread=service) as eng:
+        rid = eng.submit(lib_params(target, keep_per_traj=1), n, seed)
+        if service:
+            time.sleep(0.01)
+        else:
+            eng.step(5)
+        blob = eng.checkpoint(rid)
+        with pytest.raises(lib.FptError):
+            eng.poll(rid)             # released after the checkpoint
+    assert len(blob) > 0
+    with _engine(lib, chunk_steps=8192, traj_per_thread=1) as eng:
+        rid2 = eng.restore(blob)
+        res = eng.wait(rid2, 600.0)
+        steps = eng.per_traj_steps(rid2, n)
+        sums = eng.exact_sums(rid2)
+    ref = api.run_plain(target, n, seed).cpu().numpy()
+    assert (steps == ref).all()
+    assert res.n_used == n
+    s = stats.summarize(oracle.params_from(target), ref)
+    assert res.n_escaped == s.n_escaped
+    assert math.isclose(res.mean, s.mean, rel_tol=1e-12)
+
+
+def test_checkpoint_of_queued_request(lib, api):
+    """A request checkpointed before admission restores as a fresh run."""
+    with _engine(lib, chunk_steps=2048, max_requests=1) as eng:
+        first = eng.submit(lib_params(CONST_OVER), 1000, 1)
+        queued = eng.submit(lib_params(CONST_OVER, keep_per_traj=1), 3000, 9)
+        blob = eng.checkpoint(queued)        # still waiting for the only slot
+        rid = eng.restore(blob)
+        eng.wait(first, 600.0)
+        eng.wait(rid, 600.0)
+        steps = eng.per_traj_steps(rid, 3000)
+    assert (steps == api.run_plain(CONST_OVER, 3000, 9).cpu().numpy()).all()

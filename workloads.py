@@ -142,6 +142,29 @@ def serving_stream(n_requests: int = 200, rate_hz: float = 200.0, seed: int = 0,
     return out
 
 
+def li07_switching(n_traj: int = 30000, max_steps: int | None = None) -> dict:
+    """Switching-current workload with the device parameters the paper simulates for Fig. 10b
+    (R = 250 ohm, C = 88 fF, Ic = 0.748 uA, T = 1.2 K, 200 Hz sweep, h = 1e-4 in the paper's
+    units), mapped to engine units.  The ramp is ~3.6e-12 per paper step, ~10^11 steps to reach
+    the critical current, so a full run is hours of GPU time; tests use fewer trajectories and a
+    step budget."""
+    hbar, e2, kB = 1.054571817e-34, 2 * 1.602176634e-19, 1.380649e-23
+    R, C, Ic, T, sweep_hz, h = 250.0, 88e-15, 0.748e-6, 1.2, 200.0, 1e-4
+    E_J, E_C = hbar * Ic / e2, e2 * e2 / C
+    V0, beta, theta = E_J / E_C, hbar / (R * e2 * e2), kB * T / E_C
+    dg = 1.0 / ((0.5 / sweep_hz) / (h * hbar / E_C))        # 0 -> 1 in half a sweep period
+    s = math.sqrt(V0)
+    dt = s * h
+    nu = dg / dt
+    steps_to_one = int(math.ceil(1.0 / dg))
+    return base(model="underdamped", alpha=beta / s, D=theta / V0, gamma0=0.0, nu=nu, dt=dt,
+                threshold=2 * math.pi, threshold_mode="absolute", output="bias",
+                max_steps=max_steps or int(1.1 * steps_to_one), hist_bins=1000, hist_lo=0.0,
+                hist_hi=1.0, precision="fp32", n_traj=n_traj, seed=707,
+                paper_units={"V0": V0, "beta": beta, "theta": theta, "h": h,
+                             "delta_gamma": dg})
+
+
 def scaled(p: dict, **kw) -> dict:
     """Copy of a parameter set with some fields replaced (smaller trajectory counts or step
     budgets for the oracle-sized test cases)."""
