@@ -26,6 +26,8 @@ from . import build as _build
 
 UNDERDAMPED = 0
 OVERDAMPED = 1
+EULER = 0
+HEUN = 1
 TH_ABSOLUTE = 0
 TH_FROM_START = 1
 
@@ -34,6 +36,8 @@ class _OracleParams(ctypes.Structure):
     _fields_ = [
         ("model", ctypes.c_int32),
         ("threshold_mode", ctypes.c_int32),
+        ("integrator", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
         ("alpha", ctypes.c_double),
         ("D", ctypes.c_double),
         ("gamma0", ctypes.c_double),
@@ -69,13 +73,15 @@ class Params:
     v0: float = 0.0
     sin_amp: float = 1.0
     output_bias: bool = False      # statistics of gamma at escape (Alg. 3) instead of time
+    integrator: int = EULER
     hist_bins: int = 100
     hist_lo: float = 0.0
     hist_hi: float = 1.0
     extra: dict = field(default_factory=dict)
 
     def _c(self) -> _OracleParams:
-        return _OracleParams(int(self.model), int(self.threshold_mode), float(self.alpha),
+        return _OracleParams(int(self.model), int(self.threshold_mode), int(self.integrator), 0,
+                             float(self.alpha),
                              float(self.D), float(self.gamma0), float(self.nu),
                              float(self.sin_amp), float(self.dt), float(self.phi0),
                              float(self.v0), float(self.threshold), int(self.max_steps))
@@ -215,4 +221,5 @@ def params_from(d: dict) -> Params:
         threshold_mode=TH_ABSOLUTE if d["threshold_mode"] == "absolute" else TH_FROM_START,
         max_steps=int(d["max_steps"]), phi0=d["phi0"], v0=d["v0"], sin_amp=d["sin_amp"],
         output_bias=(d["output"] == "bias"), hist_bins=int(d["hist_bins"]),
-        hist_lo=d["hist_lo"], hist_hi=d["hist_hi"])
+        hist_lo=d["hist_lo"], hist_hi=d["hist_hi"],
+        integrator=HEUN if d.get("integrator", "em") == "heun" else EULER)

@@ -18,6 +18,10 @@
  *   - The Euler-Maruyama step of Alg. 1 (constant bias) and Alg. 3 (ramped bias), underdamped
  *     form of Eq. (JJn) in plasma-frequency units, phi'' + alpha phi' + sin phi = gamma + noise,
  *     and its overdamped counterpart phi' = gamma - sin phi + noise.
+ *   - The stochastic Heun predictor-corrector on the same model (one normal per step, drift
+ *     averaged over both ends of the step; Kloeden-Platen's weak order-2 scheme for additive
+ *     noise).  The paper integrates with the Euler scheme only (Sec. III); Heun is an option
+ *     of this implementation, pinned on its own closed forms.
  *   - The first step index k at which phi_k >= threshold (escape), or censoring at max_steps.
  */
 #include <math.h>
@@ -106,6 +110,8 @@ double oracle_normal(uint64_t seed, uint64_t traj, uint64_t n)
 typedef struct {
     int32_t model;          /* 0 = underdamped (Eq. JJn), 1 = overdamped */
     int32_t threshold_mode; /* 0 = absolute phi*, 1 = phi0 + threshold */
+    int32_t integrator;     /* 0 = Euler-Maruyama (Alg. 1), 1 = stochastic Heun */
+    int32_t reserved;
     double alpha;           /* damping (the paper's beta in plasma-frequency units) */
     double D;               /* noise intensity k_B T / E_J */
     double gamma0;          /* bias at k = 0 */
@@ -140,12 +146,19 @@ double oracle_threshold(const oracle_params *p)
 }
 
 /* One trajectory, Alg. 1 (nu = 0) or Alg. 3 (nu != 0), in FP64 with an unwrapped phase.
- * Step k (k = 1, 2, ...):
+ * Step k (k = 1, 2, ...), Euler-Maruyama:
  *   gamma_k = gamma0 + (nu*dt)*k                   (Alg. 3 sets gamma_k before the update)
  *   underdamped:  phi_k = phi_{k-1} + v_{k-1}*dt
  *                 v_k   = v_{k-1} + (-alpha*v_{k-1} - A*sin(phi_{k-1}) + gamma_k)*dt + sigma*z_k
  *   overdamped:   phi_k = phi_{k-1} + (gamma_k - A*sin(phi_{k-1}))*dt + sigma*z_k
- *   escape when phi_k >= threshold: return k.  If k reaches max_steps first: censored.
+ * Stochastic Heun (predictor-corrector with the same z_k; drift at both ends of the step, the
+ * bias taken at t_{k-1} and t_k):
+ *   overdamped:   f0 = gamma_{k-1} - A sin(phi);  p = phi + f0*dt + sigma*z
+ *                 f1 = gamma_k - A sin(p);         phi_k = phi + ((f0 + f1)*0.5)*dt + sigma*z
+ *   underdamped:  a0 = -alpha*v - A sin(phi) + gamma_{k-1};  p = phi + v*dt;  q = v + a0*dt + sigma*z
+ *                 a1 = -alpha*q - A sin(p) + gamma_k
+ *                 phi_k = phi + ((v + q)*0.5)*dt;  v_k = v + ((a0 + a1)*0.5)*dt + sigma*z
+ * Escape when phi_k >= threshold: return k.  If k reaches max_steps first: censored.
  * Returns 1 for escape (k_out = escape step) and 0 for censored (k_out = max_steps).
  * If trace_phi / trace_v are non-NULL they receive phi_k, v_k for k = 1..min(k, trace_len). */
 int oracle_trajectory_trace(const oracle_params *p, uint64_t seed, uint64_t traj,
@@ -173,7 +186,23 @@ int oracle_trajectory_trace(const oracle_params *p, uint64_t seed, uint64_t traj
         double g = p->gamma0 + nudt * (double)k;
         double s = sin(phi);
         double phi_new, v_new;
-        if (p->model == 0) {
+        if (p->integrator == 1) {
+            double g0 = p->gamma0 + nudt * (double)(k - 1);
+            if (p->model == 0) {
+                double a0 = -p->alpha * v - p->sin_amp * s + g0;
+                double pp = phi + v * p->dt;
+                double q = v + a0 * p->dt + sigma * zk;
+                double a1 = -p->alpha * q - p->sin_amp * sin(pp) + g;
+                phi_new = phi + ((v + q) * 0.5) * p->dt;
+                v_new = v + ((a0 + a1) * 0.5) * p->dt + sigma * zk;
+            } else {
+                double f0 = g0 - p->sin_amp * s;
+                double pp = phi + f0 * p->dt + sigma * zk;
+                double f1 = g - p->sin_amp * sin(pp);
+                phi_new = phi + ((f0 + f1) * 0.5) * p->dt + sigma * zk;
+                v_new = 0.0;
+            }
+        } else if (p->model == 0) {
             phi_new = phi + v * p->dt;
             v_new = v + (-p->alpha * v - p->sin_amp * s + g) * p->dt + sigma * zk;
         } else {

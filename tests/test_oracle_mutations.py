@@ -15,6 +15,7 @@ SRC = os.path.join(ROOT, "oracle", "fpt_oracle.c")
 RNG = "tests/test_oracle_rng.py"
 DYN = "tests/test_oracle_dynamics.py"
 STA = "tests/test_oracle_statistics.py"
+HEU = "tests/test_oracle_heun.py"
 
 MUTATIONS = [
     ("sin force sign (underdamped)",
@@ -47,6 +48,26 @@ MUTATIONS = [
     ("uniform offset", "((double)x + 0.5)", "((double)x + 1.0)", [RNG]),
     ("normal slot order",
      "return z[n % 4];", "return z[3 - n % 4];", [RNG]),
+    ("Heun: predictor without noise (overdamped)",
+     "double pp = phi + f0 * p->dt + sigma * zk;", "double pp = phi + f0 * p->dt;", [HEU]),
+    ("Heun: corrector drift not halved (overdamped)",
+     "phi_new = phi + ((f0 + f1) * 0.5) * p->dt + sigma * zk;",
+     "phi_new = phi + (f0 + f1) * p->dt + sigma * zk;", [HEU]),
+    ("Heun: corrector force at the old phase (overdamped)",
+     "double f1 = g - p->sin_amp * sin(pp);", "double f1 = g - p->sin_amp * s;", [HEU]),
+    ("Heun: both ends take gamma_k",
+     "nudt * (double)(k - 1);", "nudt * (double)k;", [HEU]),
+    ("Heun: predictor without noise (underdamped)",
+     "double q = v + a0 * p->dt + sigma * zk;", "double q = v + a0 * p->dt;", [HEU]),
+    ("Heun: damping at the old velocity in the corrector",
+     "double a1 = -p->alpha * q", "double a1 = -p->alpha * v", [HEU]),
+    ("Heun: phase advanced with the old velocity only",
+     "phi_new = phi + ((v + q) * 0.5) * p->dt;", "phi_new = phi + v * p->dt;", [HEU]),
+    ("Heun: corrector force at the old phase (underdamped)",
+     "- p->sin_amp * sin(pp) + g;", "- p->sin_amp * s + g;", [HEU]),
+    ("Heun: noise counted twice",
+     "phi_new = phi + ((f0 + f1) * 0.5) * p->dt + sigma * zk;",
+     "phi_new = phi + ((f0 + f1) * 0.5) * p->dt + 2.0 * sigma * zk;", [HEU]),
     ("wrong normal slot in trajectory",
      "double zk = z[n % 4];", "double zk = z[(n + 1) % 4];", [STA, DYN]),
 ]
