@@ -56,6 +56,7 @@ def parse():
     ap.add_argument("--no-flush", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-heun", action="store_true")
     ap.add_argument("--serving-requests", type=int, default=100)
     return ap.parse_args()
 
@@ -374,6 +375,39 @@ def run_ours(args):
         res32, _, _ = api.reduce(d32, st)
         fp64["fp32_plain_value"] = res32.steps_total / (ms32 / 1e3)
 
+    # the same sweep with the stochastic Heun integrator (4 XU evaluations per step: two sin of
+    # the predictor-corrector, half of the Box-Muller pair), a few engine iterations
+    heun = None
+    if not args.no_heun and rank == 0:
+        eng3 = pkg.Engine(local, chunk_steps=args.chunk_steps,
+                          traj_per_thread=args.traj_per_thread, threads_per_block=args.block)
+        st3 = torch.cuda.ExternalStream(eng3.stream, device=torch.device("cuda", local))
+        for d in pts:
+            eng3.submit(pkg.params_from(workloads.scaled(d, integrator="heun")), n_traj,
+                        d["seed"])
+        for _ in range(2):
+            eng3.step(1)
+        h0 = eng3.counters()
+        hev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(5)]
+        torch.cuda.synchronize()
+        for i in range(5):
+            if flush is not None:
+                with torch.cuda.stream(st3):
+                    flush.fill_(i & 0xFF)
+            hev[i][0].record(st3)
+            eng3.step(1)
+            hev[i][1].record(st3)
+        torch.cuda.synchronize()
+        h1 = eng3.counters()
+        hms = sum(a.elapsed_time(b) for a, b in hev)
+        hsteps = h1["useful_steps"] - h0["useful_steps"]
+        hk = h1["kernel_ms"] - h0["kernel_ms"]
+        heun = {"value": hsteps / (hms / 1e3), "unit": UNIT, "iterations": 5,
+                "kernel_gstep_s": hsteps / (hk / 1e3) / 1e9 if hk > 0 else None,
+                "xu_ops_per_step": 4.0, "integrator": "stochastic Heun, same sweep"}
+        eng3.close()
+
     serving = None
     if not args.no_serving and rank == 0 and world == 1:
         from paper_1802_05065_gb300 import serving as _srv
@@ -415,6 +449,11 @@ def run_ours(args):
                     "16 XU ops/clk/SM x N_SM x max SM clock / 3 XU ops per step"}
     if fp64:
         fp64["fp32_engine_speedup"] = per_gpu_steps_s / fp64["value"]
+    if heun and heun["kernel_gstep_s"]:
+        hpeak = 16.0 * n_sm * f_max * 1e6 / 4.0
+        heun["roofline"] = {"bound": "alu", "achieved": heun["kernel_gstep_s"],
+                            "peak": hpeak / 1e9, "unit": "Gstep/s",
+                            "frac": heun["kernel_gstep_s"] * 1e9 / hpeak}
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / max(args.steps, 1),
@@ -435,8 +474,9 @@ def run_ours(args):
         "e2e": e2e,
         "fp64_plain": fp64,
         "fp32_engine_point": fast_point,
+        "heun": heun,
         "serving": serving,
-        "gpu_launches": 2 * args.steps,
+        "gpu_launches": 2 * args.steps,   # chunk + scan per timed iteration
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

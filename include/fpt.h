@@ -47,7 +47,12 @@ typedef enum {
 
 enum { FPT_UNDERDAMPED = 0, FPT_OVERDAMPED = 1 };
 enum { FPT_FP32 = 0, FPT_FP64 = 1 };
-enum { FPT_EULER_MARUYAMA = 0 };
+/* Integrators.  FPT_EULER_MARUYAMA is the Euler scheme of Alg. 1 / Alg. 3.  FPT_HEUN is the
+ * stochastic Heun predictor-corrector (one normal per step, drift averaged over both ends of the
+ * step, bias taken at t_{k-1} and t_k): weak order 2 for the additive noise of Eq. (JJn).  The
+ * paper integrates with Euler only; Heun is an option of this library, on the same random
+ * stream (step k still draws normal k-1). */
+enum { FPT_EULER_MARUYAMA = 0, FPT_HEUN = 1 };
 enum { FPT_OUT_TIME = 0, FPT_OUT_BIAS = 1 };
 enum { FPT_TH_ABSOLUTE = 0, FPT_TH_FROM_START = 1 };
 
@@ -56,7 +61,7 @@ enum { FPT_TH_ABSOLUTE = 0, FPT_TH_FROM_START = 1 };
 typedef struct {
     int32_t model;          /* FPT_UNDERDAMPED | FPT_OVERDAMPED */
     int32_t precision;      /* FPT_FP32 (engine, plain kernel) | FPT_FP64 (plain kernel only) */
-    int32_t integrator;     /* FPT_EULER_MARUYAMA */
+    int32_t integrator;     /* FPT_EULER_MARUYAMA | FPT_HEUN */
     int32_t output;         /* FPT_OUT_TIME: x = k*dt; FPT_OUT_BIAS: x = gamma0 + nu*dt*k */
     int32_t threshold_mode; /* FPT_TH_ABSOLUTE: phi* = threshold; FPT_TH_FROM_START: phi0 + threshold */
     int32_t keep_per_traj;  /* engine: 1 keeps every escape step for fpt_per_traj */
@@ -65,7 +70,7 @@ typedef struct {
     double gamma0;          /* bias at t = 0 */
     double nu;              /* bias ramp per unit time (0 = constant bias) */
     double sin_amp;         /* A: amplitude of the sin term (1 = junction; 0 = free drift) */
-    double dt;              /* Euler step h > 0 */
+    double dt;              /* integration step h > 0 */
     double phi0;            /* start phase; NaN = arcsin(gamma0) (Alg. 1, 3; needs abs(gamma0) <= 1) */
     double v0;              /* start velocity (underdamped) */
     double threshold;       /* see threshold_mode; must exceed the start phase */

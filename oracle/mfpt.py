@@ -148,3 +148,25 @@ def slow_passage_delay(nu: float) -> float:
     from scipy.special import ai_zeros
     a1 = abs(float(ai_zeros(1)[0][0]))
     return 2.0 ** (1.0 / 3.0) * a1 * nu ** (2.0 / 3.0)
+
+
+def adiabatic_switching_cdf(gammas, gamma0: float, nu: float, D: float, dt: float | None = None,
+                            A: float = 1.0) -> np.ndarray:
+    """Switching-bias distribution of a slow linear ramp in the adiabatic approximation that the
+    paper compares with (Sec. IV.B, Fig. 10b; Fulton and Dunkleberger): escape is a Poisson
+    process whose rate at bias g is the constant-bias rate 1 / T(g), so
+
+        P(gamma_sw <= g) = 1 - exp(-(1/nu) Int_{gamma0}^{g} dg' / T(g')),
+
+    with T the exact overdamped MFPT (plus the discrete-monitoring delay when dt is given).
+    Valid for g < 1 and ramps slow against the relaxation in the well.  `gammas` must be
+    increasing, start at gamma0 and stay below 1; the integral is taken by the trapezoid rule
+    on that grid."""
+    g = np.asarray(gammas, dtype=np.float64)
+    if g[0] != gamma0 or np.any(np.diff(g) <= 0) or g[-1] >= A:
+        raise ValueError("grid must start at gamma0, increase, and stay below the critical bias")
+    T = np.array([overdamped_mfpt(x, D, A) + (monitoring_shift(x, D, dt, A) if dt else 0.0)
+                  for x in g])
+    rate = 1.0 / (nu * T)
+    H = np.concatenate([[0.0], np.cumsum(0.5 * (rate[1:] + rate[:-1]) * np.diff(g))])
+    return -np.expm1(-H)

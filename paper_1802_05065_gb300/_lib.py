@@ -17,6 +17,7 @@ SELFTEST_PATH = os.path.join(HERE, "_build", "libfpt_selftest.so")
 OK, PENDING, EINVAL, ENOMEM, EBUSY, ENOTFOUND, ETIMEDOUT, ECUDA, EFULL = 0, 1, -1, -2, -3, -4, -5, -6, -7
 UNDERDAMPED, OVERDAMPED = 0, 1
 FP32, FP64 = 0, 1
+EULER_MARUYAMA, HEUN = 0, 1
 OUT_TIME, OUT_BIAS = 0, 1
 TH_ABSOLUTE, TH_FROM_START = 0, 1
 
@@ -157,7 +158,7 @@ def params_from(d: dict, **over) -> Params:
     p = Params()
     p.model = UNDERDAMPED if d["model"] == "underdamped" else OVERDAMPED
     p.precision = FP64 if d.get("precision", "fp32") == "fp64" else FP32
-    p.integrator = 0
+    p.integrator = HEUN if d.get("integrator", "em") == "heun" else EULER_MARUYAMA
     p.output = OUT_BIAS if d.get("output", "time") == "bias" else OUT_TIME
     p.threshold_mode = TH_FROM_START if d.get("threshold_mode") == "from_start" else TH_ABSOLUTE
     p.keep_per_traj = int(bool(d.get("keep_per_traj", 0)))

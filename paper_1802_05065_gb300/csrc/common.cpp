@@ -28,7 +28,8 @@ bool decode(const fpt_params *p, Decoded *d, std::string *err) {
     if (!p) return fail("params is NULL");
     if (p->model != FPT_UNDERDAMPED && p->model != FPT_OVERDAMPED) return fail("unknown model");
     if (p->output != FPT_OUT_TIME && p->output != FPT_OUT_BIAS) return fail("unknown output");
-    if (p->integrator != FPT_EULER_MARUYAMA) return fail("unknown integrator");
+    if (p->integrator != FPT_EULER_MARUYAMA && p->integrator != FPT_HEUN)
+        return fail("unknown integrator");
     if (p->threshold_mode != FPT_TH_ABSOLUTE && p->threshold_mode != FPT_TH_FROM_START)
         return fail("unknown threshold_mode");
     if (!(p->dt > 0) || !finite(p->dt)) return fail("dt must be positive and finite");
@@ -48,6 +49,8 @@ bool decode(const fpt_params *p, Decoded *d, std::string *err) {
     if (!std::isnan(p->phi0) && !finite(p->phi0)) return fail("phi0 must be finite or NaN");
 
     d->model = p->model;
+    d->integrator = p->integrator;
+    d->kind = p->model + 2 * p->integrator;
     d->output = p->output;
     d->alpha = p->model == FPT_UNDERDAMPED ? p->alpha : 0.0;
     d->D = p->D;
@@ -71,7 +74,8 @@ bool decode(const fpt_params *p, Decoded *d, std::string *err) {
 
     // single precision
     d->dt_f = static_cast<float>(d->dt);
-    d->A_f = static_cast<float>(1.0 - d->alpha * d->dt);
+    d->A_f = d->integrator == FPT_HEUN ? static_cast<float>(-d->alpha)
+                                       : static_cast<float>(1.0 - d->alpha * d->dt);
     d->amp_f = static_cast<float>(d->amp);
     d->bmc_f = static_cast<float>(-2.0 * M_LN2 * d->sigma * d->sigma);
     d->nudt_f = static_cast<float>(d->nudt);

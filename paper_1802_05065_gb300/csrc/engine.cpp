@@ -112,7 +112,7 @@ struct fpt_engine {
     SlotDev *h_slots = nullptr;
     SlotCtl *h_ctl = nullptr, *h_ctl_init = nullptr;
     int *h_caps = nullptr, *h_act = nullptr, *h_act_count = nullptr;
-    int *h_preempt = nullptr, *h_flags = nullptr;   // flags: vacate[2], strict
+    int *h_preempt = nullptr, *h_flags = nullptr;   // flags: vacate[kNumKinds], strict
     uint64_t preempted = 0;
     unsigned long long *h_counters = nullptr;
     int *h_state = nullptr;
@@ -220,7 +220,7 @@ fpt_status admit(fpt_engine *e) {
         S.r0 = d.r0_f;
         S.eb0 = d.eb0_f;
         S.w0 = d.w0;
-        S.model = d.model;
+        S.kind = d.kind;
         S.key0 = static_cast<uint32_t>(R.seed);
         S.key1 = static_cast<uint32_t>(R.seed >> 32);
         S.traj_offset = R.params.traj_offset;
@@ -289,10 +289,10 @@ fpt_status admit(fpt_engine *e) {
 // Fair share = lanes / running requests.  A request is starved when it has work (unclaimed
 // ids or suspended trajectories) and holds less than half of min(share, its demand).  While
 // anyone is starved: caps are strict, requests above their share suspend the excess lanes at
-// the end of the launch, and if a starved request's model differs, whole warps of the other
-// model vacate so they can switch.
+// the end of the launch, and if a starved request's kind (model x integrator) differs, whole
+// warps of other kinds vacate so they can switch.
 void build_lists(fpt_engine *e) {
-    int cnt[2] = {0, 0};
+    int cnt[kNumKinds] = {0, 0, 0, 0};
     int active = 0;
     for (int s = 0; s < e->maxr; ++s) {
         e->h_preempt[s] = 0;
@@ -303,20 +303,19 @@ void build_lists(fpt_engine *e) {
             e->h_preempt[s] = 1 << 30;
             continue;
         }
-        e->h_act[R.dec.model * e->maxr + cnt[R.dec.model]++] = s;
+        e->h_act[R.dec.kind * e->maxr + cnt[R.dec.kind]++] = s;
         ++active;
     }
-    e->h_act_count[0] = cnt[0];
-    e->h_act_count[1] = cnt[1];
+    for (int k = 0; k < kNumKinds; ++k) e->h_act_count[k] = cnt[k];
     const int share = active ? static_cast<int>((e->lanes + active - 1) / active) : 0;
     const int cap = active ? share + 32 : 0;
     for (int s = 0; s < e->maxr; ++s) e->h_caps[s] = cap;
-    e->h_flags[0] = e->h_flags[1] = e->h_flags[2] = 0;
+    for (int k = 0; k <= kNumKinds; ++k) e->h_flags[k] = 0;
     for (int s = 0; s < e->maxr; ++s)
-        if (e->h_preempt[s]) e->h_flags[2] = 1;   // keep a suspending request's lanes from refilling
+        if (e->h_preempt[s]) e->h_flags[kNumKinds] = 1;   // keep a suspending request's lanes from refilling
     if (active < 2) return;
-    int64_t deficit[2] = {0, 0};
-    bool over[2] = {false, false};
+    int64_t deficit[kNumKinds] = {0, 0, 0, 0};
+    bool over[kNumKinds] = {false, false, false, false};
     for (int s = 0; s < e->maxr; ++s) {
         if (!e->slot_req[s]) continue;
         Request &R = *e->reqs[e->slot_req[s]];
@@ -326,11 +325,13 @@ void build_lists(fpt_engine *e) {
         const int64_t unclaimed = C.head < R.n_traj ? static_cast<int64_t>(R.n_traj - C.head) : 0;
         const int64_t remaining = unclaimed + std::max(C.park_avail, 0);
         const int64_t want = std::min<int64_t>(share, C.inflight + remaining);
-        if (remaining > 0 && C.inflight < want / 2) deficit[R.dec.model] += want - C.inflight;
-        if (C.inflight > share) over[R.dec.model] = true;
+        if (remaining > 0 && C.inflight < want / 2) deficit[R.dec.kind] += want - C.inflight;
+        if (C.inflight > share) over[R.dec.kind] = true;
     }
-    if (deficit[0] + deficit[1] == 0) return;
-    e->h_flags[2] = 1;   // strict caps
+    int64_t total_deficit = 0;
+    for (int k = 0; k < kNumKinds; ++k) total_deficit += deficit[k];
+    if (total_deficit == 0) return;
+    e->h_flags[kNumKinds] = 1;   // strict caps
     for (int s = 0; s < e->maxr; ++s) {
         if (!e->slot_req[s]) continue;
         Request &R = *e->reqs[e->slot_req[s]];
@@ -342,9 +343,11 @@ void build_lists(fpt_engine *e) {
         e->preempted += static_cast<uint64_t>(e->h_preempt[s]);
     }
     const int64_t lanes_per_warp = 32ll * e->T;
-    for (int m = 0; m < 2; ++m)
-        if (deficit[1 - m] > 0 && over[m])
-            e->h_flags[m] = static_cast<int>((deficit[1 - m] + lanes_per_warp - 1) / lanes_per_warp);
+    for (int m = 0; m < kNumKinds; ++m) {
+        const int64_t others = total_deficit - deficit[m];
+        if (others > 0 && over[m])
+            e->h_flags[m] = static_cast<int>((others + lanes_per_warp - 1) / lanes_per_warp);
+    }
 }
 
 fpt_status enqueue_iteration(fpt_engine *e) {
@@ -354,9 +357,12 @@ fpt_status enqueue_iteration(fpt_engine *e) {
     }
     CK(cudaMemcpyAsync(e->d_caps, e->h_caps, e->maxr * sizeof(int), cudaMemcpyHostToDevice, e->stream));
     CK(cudaMemcpyAsync(e->d_preempt, e->h_preempt, e->maxr * sizeof(int), cudaMemcpyHostToDevice, e->stream));
-    CK(cudaMemcpyAsync(e->d_vacate, e->h_flags, 3 * sizeof(int), cudaMemcpyHostToDevice, e->stream));
-    CK(cudaMemcpyAsync(e->d_act, e->h_act, 2 * e->maxr * sizeof(int), cudaMemcpyHostToDevice, e->stream));
-    CK(cudaMemcpyAsync(e->d_act_count, e->h_act_count, 2 * sizeof(int), cudaMemcpyHostToDevice, e->stream));
+    CK(cudaMemcpyAsync(e->d_vacate, e->h_flags, (kNumKinds + 1) * sizeof(int), cudaMemcpyHostToDevice,
+                       e->stream));
+    CK(cudaMemcpyAsync(e->d_act, e->h_act, kNumKinds * e->maxr * sizeof(int), cudaMemcpyHostToDevice,
+                       e->stream));
+    CK(cudaMemcpyAsync(e->d_act_count, e->h_act_count, kNumKinds * sizeof(int), cudaMemcpyHostToDevice,
+                       e->stream));
     const unsigned evflags = e->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     CK(cudaEventRecordWithFlags(e->ev_k0, e->stream, evflags));
     CK(launch_engine_chunk(e->dev, e->T, e->grid, e->block, e->stream));
@@ -560,12 +566,12 @@ fpt_status create_impl(const fpt_engine_config *cfg_in, fpt_engine *e) {
     CK(cudaMalloc(&e->d_slots, R * sizeof(SlotDev)));
     CK(cudaMalloc(&e->d_ctl, R * sizeof(SlotCtl)));
     CK(cudaMalloc(&e->d_caps, R * sizeof(int)));
-    CK(cudaMalloc(&e->d_act, 2 * R * sizeof(int)));
-    CK(cudaMalloc(&e->d_act_count, 2 * sizeof(int)));
+    CK(cudaMalloc(&e->d_act, kNumKinds * R * sizeof(int)));
+    CK(cudaMalloc(&e->d_act_count, kNumKinds * sizeof(int)));
     CK(cudaMalloc(&e->d_preempt, R * sizeof(int)));
-    CK(cudaMalloc(&e->d_vacate, 3 * sizeof(int)));   // vacate[2], strict
+    CK(cudaMalloc(&e->d_vacate, (kNumKinds + 1) * sizeof(int)));   // vacate[kNumKinds], strict
     CK(cudaMemsetAsync(e->d_preempt, 0, R * sizeof(int), e->stream));
-    CK(cudaMemsetAsync(e->d_vacate, 0, 3 * sizeof(int), e->stream));
+    CK(cudaMemsetAsync(e->d_vacate, 0, (kNumKinds + 1) * sizeof(int), e->stream));
     const size_t L = e->lanes;
     CK(cudaMalloc(&e->d_lane_mem, L * 4 * 10));
     const unsigned nwarps = static_cast<unsigned>(e->grid) * e->block / 32;
@@ -599,17 +605,17 @@ fpt_status create_impl(const fpt_engine_config *cfg_in, fpt_engine *e) {
     CK(cudaMallocHost(&e->h_ctl, R * sizeof(SlotCtl)));
     CK(cudaMallocHost(&e->h_ctl_init, R * sizeof(SlotCtl)));
     CK(cudaMallocHost(&e->h_caps, R * sizeof(int)));
-    CK(cudaMallocHost(&e->h_act, 2 * R * sizeof(int)));
-    CK(cudaMallocHost(&e->h_act_count, 2 * sizeof(int)));
+    CK(cudaMallocHost(&e->h_act, kNumKinds * R * sizeof(int)));
+    CK(cudaMallocHost(&e->h_act_count, kNumKinds * sizeof(int)));
     CK(cudaMallocHost(&e->h_preempt, R * sizeof(int)));
-    CK(cudaMallocHost(&e->h_flags, 3 * sizeof(int)));
+    CK(cudaMallocHost(&e->h_flags, (kNumKinds + 1) * sizeof(int)));
     std::memset(e->h_preempt, 0, R * sizeof(int));
-    std::memset(e->h_flags, 0, 3 * sizeof(int));
+    std::memset(e->h_flags, 0, (kNumKinds + 1) * sizeof(int));
     CK(cudaMallocHost(&e->h_counters, kCntCount * sizeof(unsigned long long)));
     std::memset(e->h_ctl, 0, R * sizeof(SlotCtl));
     std::memset(e->h_caps, 0, R * sizeof(int));
-    std::memset(e->h_act, 0, 2 * R * sizeof(int));
-    std::memset(e->h_act_count, 0, 2 * sizeof(int));
+    std::memset(e->h_act, 0, kNumKinds * R * sizeof(int));
+    std::memset(e->h_act_count, 0, kNumKinds * sizeof(int));
     std::memset(e->h_counters, 0, kCntCount * sizeof(unsigned long long));
     e->slot_req.assign(R, 0);
     EngineDev &d = e->dev;
@@ -619,7 +625,7 @@ fpt_status create_impl(const fpt_engine_config *cfg_in, fpt_engine *e) {
     d.act_list = e->d_act;
     d.preempt = e->d_preempt;
     d.vacate = e->d_vacate;
-    d.strict = e->d_vacate + 2;
+    d.strict = e->d_vacate + kNumKinds;
     d.act_count = e->d_act_count;
     d.warp_kind = e->d_warp_kind;
     d.warp_cursor = e->d_warp_cursor;

@@ -17,6 +17,10 @@ namespace fpt {
 
 enum : int { kSlotFree = 0, kSlotActive = 1, kSlotFinished = 2, kSlotCancelled = 3 };
 
+// Code paths a warp can run: kind = model + 2 x integrator (underdamped / overdamped x
+// Euler-Maruyama / Heun).  A warp runs one kind at a time.
+constexpr int kNumKinds = 4;
+
 // Blocks (of 4 steps) between re-bases of a trajectory's single-precision bias: gamma_k is
 // formed as gs + nu dt (s + 1) with gs = gb + nu dt Jf and gb = gamma0 + nu dt 4 c_base in FP64,
 // c_base the trajectory's own block count rounded down to a multiple of kRebaseBlocks, so the
@@ -40,7 +44,7 @@ struct IdBlockAcc {
 struct SlotDev {
     // single-precision step constants
     float dt, A, amp, bmc, nudt, v0, r0, eb0;
-    int32_t w0, model;
+    int32_t w0, kind;         // kind = model + 2 x integrator
     uint32_t key0, key1;
     // trajectories and budget
     uint64_t traj_offset, n_traj, max_steps, nblocks;   // nblocks = ceil(max_steps / 4)
@@ -85,12 +89,12 @@ struct EngineDev {
     SlotCtl *ctl;
     const int *caps;        // [max_requests] fair-share lane caps
     int *preempt;           // [max_requests] lanes to suspend at the end of this launch
-    int *vacate;            // [2] whole warps of each model to suspend at the end of this launch
+    int *vacate;            // [kNumKinds] whole warps of each kind to suspend at the end of this launch
     const int *strict;      // [1] 1: never exceed the caps (someone is starved)
-    const int *act_list;    // [2][max_requests] claimable slots per model
-    const int *act_count;   // [2]
+    const int *act_list;    // [kNumKinds][max_requests] claimable slots per kind
+    const int *act_count;   // [kNumKinds]
     LaneSoA lanes;
-    int *warp_kind;         // model each warp currently integrates (-1 idle)
+    int *warp_kind;         // kind each warp currently integrates (-1 idle)
     unsigned int *warp_cursor;
     unsigned long long *counters;
     unsigned int chunk_blocks;

@@ -1,8 +1,8 @@
 // engine_kernels.cu -- the persistent batched FPT kernel and the completion scan.
 //
-// One launch ("chunk") advances every resident lane by up to chunk_blocks x 4 Euler-Maruyama
-// steps.  A lane integrates one trajectory: Philox4x32-10 -> Box-Muller -> step (Alg. 1 / 3)
-// on a phase wrapped to [-pi, pi) with an integer winding count.  Escape and upper-wrap events
+// One launch ("chunk") advances every resident lane by up to chunk_blocks x 4 steps
+// (Euler-Maruyama or stochastic Heun).  A lane integrates one trajectory: Philox4x32-10 ->
+// Box-Muller -> step (Alg. 1 / 3) on a phase wrapped to [-pi, pi) with an integer winding count.  Escape and upper-wrap events
 // are caught by one compare per step (r >= hb); the lower wrap (r < -pi) is applied at the end
 // of each 4-step block.  At the block end the warp votes, finished lanes publish their exact
 // result and the warp refills them -- first with suspended trajectories, then with new ids from
@@ -14,8 +14,8 @@
 // resumes it exactly.  The ramped bias is formed from the trajectory's own step count, so a
 // trajectory's arithmetic never depends on which lane, launch or schedule ran it.
 //
-// A warp integrates one model at a time (underdamped or overdamped code path); the request of
-// each lane is free, so requests of the same model share warps.  Refill is round-robin over
+// A warp integrates one kind at a time (model x integrator: four code paths); the request of
+// each lane is free, so requests of the same kind share warps.  Refill is round-robin over
 // the claimable requests with a fair-share cap on in-flight lanes per request (first pass),
 // then without cap (second pass), so no lane idles while any request has work.
 #include <cstdint>
@@ -227,7 +227,7 @@ __device__ __forceinline__ void finish_lanes(Lane (&L)[T], const EngineDev &E, u
     }
 }
 
-// Warp-collective refill of idle lanes with trajectories of requests of model `kind`.
+// Warp-collective refill of idle lanes with trajectories of requests of kind `kind`.
 template <int T>
 __device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, int kind, int &n_active,
                                        unsigned &cursor) {
@@ -317,9 +317,9 @@ __device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, int kin
     }
 }
 
-// Integrate blocks of 4 steps with model M until the launch's block count is reached or the
-// whole warp has run out of work.  Returns the next block index.
-template <int M, int T>
+// Integrate blocks of 4 steps with model M and integrator H until the launch's block count is
+// reached or the whole warp has run out of work.  Returns the next block index.
+template <int M, int H, int T>
 __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E, unsigned b, int &n_active,
                                unsigned &cursor, unsigned long long &useful, unsigned &n_esc,
                                unsigned &n_cens) {
@@ -349,9 +349,10 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
         for (int s = 0; s < 4; ++s) {
 #pragma unroll
             for (int t = 0; t < T; ++t) {
-                step_f32<M>(L[t].r, L[t].v, rr[t][s >> 1], tg[t][s],
-                            fmaf(L[t].nudt, static_cast<float>(s + 1), gs[t]), L[t].dt, L[t].A,
-                            L[t].amp);
+                step_f32<M, H>(L[t].r, L[t].v, rr[t][s >> 1], tg[t][s],
+                               fmaf(L[t].nudt, static_cast<float>(s), gs[t]),
+                               fmaf(L[t].nudt, static_cast<float>(s + 1), gs[t]), L[t].dt, L[t].A,
+                               L[t].amp);
                 mx[t] = fmaxf(mx[t], L[t].r);
             }
         }
@@ -375,9 +376,10 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
                     L[t].v = v0s[t];
 #pragma unroll
                     for (int s = 0; s < 4; ++s) {
-                        step_f32<M>(L[t].r, L[t].v, rr[t][s >> 1], tg[t][s],
-                                    fmaf(L[t].nudt, static_cast<float>(s + 1), gs[t]), L[t].dt,
-                                    L[t].A, L[t].amp);
+                        step_f32<M, H>(L[t].r, L[t].v, rr[t][s >> 1], tg[t][s],
+                                       fmaf(L[t].nudt, static_cast<float>(s), gs[t]),
+                                       fmaf(L[t].nudt, static_cast<float>(s + 1), gs[t]), L[t].dt,
+                                       L[t].A, L[t].amp);
                         if (L[t].r >= L[t].hb) phase_event(L[t], E, s);
                     }
                 }
@@ -385,7 +387,7 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
                 if (L[t].slot >= 0 && L[t].c_lo == 0u) L[t].c_hi += 1u;   // 2^32-block carry
             }
             finish_lanes(L, E, useful, n_active, n_esc, n_cens);
-            refill(L, E, M, n_active, cursor);
+            refill(L, E, M + 2 * H, n_active, cursor);
             if (!__any_sync(kFull, n_active > 0)) break;
         }
     }
@@ -436,21 +438,32 @@ __global__ void __launch_bounds__(256) engine_chunk_kernel(EngineDev E) {
     unsigned b = 0;
     while (b < E.chunk_blocks) {
         if (kind < 0) {
-            const int first = static_cast<int>(warp & 1u);
-            for (int q = 0; q < 2 && kind < 0; ++q) {
-                const int m = first ^ q;
+            // an idle warp looks for work of any kind, starting from a warp-dependent one
+            const int first = static_cast<int>(warp % kNumKinds);
+            for (int q = 0; q < kNumKinds && kind < 0; ++q) {
+                const int m = (first + q) % kNumKinds;
                 refill(L, E, m, n_active, cursor);
                 if (__any_sync(kFull, n_active > 0)) kind = m;
             }
             if (kind < 0) break;
         }
-        if (kind == kUnder)
-            b = run_blocks<kUnder, T>(L, E, b, n_active, cursor, useful, n_esc, n_cens);
-        else
-            b = run_blocks<kOver, T>(L, E, b, n_active, cursor, useful, n_esc, n_cens);
+        switch (kind) {
+        case kUnder + 2 * kEuler:
+            b = run_blocks<kUnder, kEuler, T>(L, E, b, n_active, cursor, useful, n_esc, n_cens);
+            break;
+        case kOver + 2 * kEuler:
+            b = run_blocks<kOver, kEuler, T>(L, E, b, n_active, cursor, useful, n_esc, n_cens);
+            break;
+        case kUnder + 2 * kHeun:
+            b = run_blocks<kUnder, kHeun, T>(L, E, b, n_active, cursor, useful, n_esc, n_cens);
+            break;
+        default:
+            b = run_blocks<kOver, kHeun, T>(L, E, b, n_active, cursor, useful, n_esc, n_cens);
+            break;
+        }
         if (!__any_sync(kFull, n_active > 0)) kind = -1;
     }
-    // Preemption: a whole warp of this model may be asked to vacate (so it can switch model),
+    // Preemption: a whole warp of this kind may be asked to vacate (so it can switch kind),
     // or single lanes of requests above their share to suspend.  Suspended state goes to the
     // request's ring; a push needs a free ring entry (park_used < park_cap).
     bool vacate = false;

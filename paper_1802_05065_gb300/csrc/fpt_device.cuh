@@ -3,7 +3,8 @@
 //   philox4x32_10   counter-based generator (Salmon et al., SC'11), all in registers
 //   bm_pair_f32     Box-Muller (Sec. III.B, nrand) in single precision, noise-scaled
 //   bm_pair_f64     Box-Muller in double precision, same arithmetic order as the FP64 oracle
-//   step_f32<M>     one Euler-Maruyama step of Alg. 1 / Alg. 3 on a wrapped phase
+//   step_f32<M,H>   one Euler-Maruyama step of Alg. 1 / Alg. 3 (H = 0) or one stochastic Heun
+//                   step (H = 1) on a wrapped phase
 //
 // Keying (fixed once for the whole library): key = (seed lo, seed hi), counter =
 // (block lo, block hi, trajectory lo, trajectory hi); block b feeds steps 4b+1 .. 4b+4, words
@@ -106,31 +107,59 @@ __device__ __forceinline__ void bm_pair_f64(uint32_t x0, uint32_t x1, double &z0
 // Per-lane constants of the FP32 step, decoded from a request on the host (set-up of Alg. 1).
 struct StepConstF32 {
     float dt;     // h
-    float A;      // 1 - alpha dt (underdamped velocity decay)
+    float A;      // underdamped velocity coefficient: 1 - alpha dt (Euler), -alpha (Heun)
     float amp;    // amplitude of the sin term
     float bmc;    // -2 ln 2 sigma^2 (Box-Muller radius in log2 form)
     float nudt;   // bias increment per step (Alg. 3: delta-gamma)
 };
 
 enum : int { kUnder = 0, kOver = 1 };
+enum : int { kEuler = 0, kHeun = 1 };
 
-// One Euler-Maruyama step with noise increment sigma z = rr * trig and bias g = gamma_k:
-//   underdamped: phi += v dt;  v = (1 - alpha dt) v + (g - A sin phi_old) dt + sigma z
-//   overdamped : phi += (g - A sin phi_old) dt + sigma z
-// Both updates read the state of the previous step (the Euler update of Alg. 1).  r is the phase
-// wrapped to [-pi, pi); the caller restores the range and counts windings.  Every rounding is
-// explicit (fmaf / __fmul_rn), so all kernels that take this step agree bit for bit.
-template <int M>
-__device__ __forceinline__ void step_f32(float &r, float &v, float rr, float trig, float g,
-                                         float dt, float A, float amp) {
-    const float s = __sinf(r);
-    const float f = fmaf(-amp, s, g);
-    if constexpr (M == kUnder) {
-        const float vn = fmaf(A, v, fmaf(dt, f, __fmul_rn(rr, trig)));
-        r = fmaf(dt, v, r);
-        v = vn;
+// One step with noise increment sigma z = rr * trig; g0 = gamma_{k-1}, g1 = gamma_k; amp is the
+// amplitude of the sin term and A the underdamped velocity coefficient.
+// Euler-Maruyama (H = 0; Alg. 1 / Alg. 3, both updates read the state of the previous step):
+//   underdamped: phi += v dt;  v = A v + (g1 - amp sin phi_old) dt + sigma z     [A = 1 - alpha dt]
+//   overdamped : phi += (g1 - amp sin phi_old) dt + sigma z
+// Stochastic Heun (H = 1; predictor with the step's normal, corrector averaging the drift over
+// both ends of the step):
+//   overdamped : f0 = g0 - amp sin phi;  p = phi + f0 dt + sigma z;  f1 = g1 - amp sin p
+//                phi += (f0 + f1) dt / 2 + sigma z
+//   underdamped: a0 = A v - amp sin phi + g0;  p = phi + v dt;  q = v + a0 dt + sigma z
+//                a1 = A q - amp sin p + g1;  phi += (v + q) dt / 2;  v += (a0 + a1) dt / 2 + sigma z
+//                                                                               [A = -alpha]
+// r is the phase wrapped to [-pi, pi); the caller restores the range and counts windings.
+// Every rounding is explicit (fmaf / __fmul_rn / __fadd_rn), so all kernels that take this step
+// agree bit for bit.
+template <int M, int H>
+__device__ __forceinline__ void step_f32(float &r, float &v, float rr, float trig, float g0,
+                                         float g1, float dt, float A, float amp) {
+    if constexpr (H == kEuler) {
+        const float s = __sinf(r);
+        const float f = fmaf(-amp, s, g1);
+        if constexpr (M == kUnder) {
+            const float vn = fmaf(A, v, fmaf(dt, f, __fmul_rn(rr, trig)));
+            r = fmaf(dt, v, r);
+            v = vn;
+        } else {
+            r = fmaf(rr, trig, fmaf(dt, f, r));
+        }
     } else {
-        r = fmaf(rr, trig, fmaf(dt, f, r));
+        const float n = __fmul_rn(rr, trig);
+        const float hdt = __fmul_rn(0.5f, dt);
+        if constexpr (M == kUnder) {
+            const float a0 = fmaf(A, v, fmaf(-amp, __sinf(r), g0));
+            const float p = fmaf(dt, v, r);
+            const float q = __fadd_rn(fmaf(dt, a0, v), n);
+            const float a1 = fmaf(A, q, fmaf(-amp, __sinf(p), g1));
+            r = fmaf(hdt, __fadd_rn(v, q), r);
+            v = __fadd_rn(fmaf(hdt, __fadd_rn(a0, a1), v), n);
+        } else {
+            const float f0 = fmaf(-amp, __sinf(r), g0);
+            const float p = __fadd_rn(fmaf(dt, f0, r), n);
+            const float f1 = fmaf(-amp, __sinf(p), g1);
+            r = __fadd_rn(fmaf(hdt, __fadd_rn(f0, f1), r), n);
+        }
     }
 }
 

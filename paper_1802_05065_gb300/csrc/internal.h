@@ -25,6 +25,8 @@ constexpr int kMaxBins = 1 << 20;
 //   nudt = nu dt,  phi0 = asin(gamma0) when not given,  phi* = phi0 + threshold or threshold.
 struct Decoded {
     int model = 0, output = 0;
+    int integrator = 0;  // FPT_EULER_MARUYAMA | FPT_HEUN
+    int kind = 0;        // model + 2 integrator: the code path a warp runs
     double alpha = 0, D = 0, gamma0 = 0, nudt = 0, amp = 1, dt = 0, sigma = 0;
     double phi0 = 0, v0 = 0, th = 0;
     uint64_t max_steps = 0;
@@ -32,7 +34,8 @@ struct Decoded {
     double out_a = 0, out_b = 0;
     int hist_bins = 1;
     double hist_lo = 0, hist_hi = 1, hist_inv_w = 1;
-    // single-precision step constants and the wrapped start / threshold
+    // single-precision step constants and the wrapped start / threshold; A_f is the underdamped
+    // velocity coefficient, 1 - alpha dt for Euler and -alpha for Heun
     float dt_f = 0, A_f = 0, amp_f = 0, bmc_f = 0, nudt_f = 0, v0_f = 0;
     float r0_f = 0;      // start phase wrapped to [-pi, pi)
     int32_t w0 = 0;      // windings of the start phase
@@ -52,7 +55,7 @@ void sums_to_result(const Decoded &d, const fpt_sums &s, fpt_result *out);
 
 // ---- kernels (launch wrappers; definitions in plain.cu / engine_kernels.cu) ----
 struct PlainArgs {
-    int model;
+    int model, integrator;
     uint32_t key0, key1;
     uint64_t traj0, n;
     int64_t *steps;

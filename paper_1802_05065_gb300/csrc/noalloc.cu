@@ -92,7 +92,7 @@ __device__ __forceinline__ void nl_claim(NLane &L, const NoAllocArgs &a, unsigne
     }
 }
 
-template <int M>
+template <int M, int H>
 __global__ void __launch_bounds__(kBlock) noalloc_kernel(NoAllocArgs a) {
     extern __shared__ unsigned int sh_hist[];
     __shared__ unsigned long long sh_sums[8];   // done, escaped, s1 lo/hi, s2 lo/hi, under, over
@@ -126,8 +126,8 @@ __global__ void __launch_bounds__(kBlock) noalloc_kernel(NoAllocArgs a) {
         const float gs = fmaf(a.nudt, L.Jf, L.gb);
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
-            step_f32<M>(L.r, L.v, rr[s >> 1], tg[s], fmaf(a.nudt, static_cast<float>(s + 1), gs),
-                        a.dt, a.A, a.amp);
+            step_f32<M, H>(L.r, L.v, rr[s >> 1], tg[s], fmaf(a.nudt, static_cast<float>(s), gs),
+                           fmaf(a.nudt, static_cast<float>(s + 1), gs), a.dt, a.A, a.amp);
             if (L.r >= L.hb) {
                 const float eb = fmaf(-kTwoPiF, static_cast<float>(L.w - a.w0), a.eb0);
                 if (L.r >= eb) {
@@ -304,10 +304,12 @@ extern "C" fpt_status fpt_run_noalloc(const fpt_params *params, uint64_t n_traj,
         set_error("fpt_run_noalloc: hist_bins must be <= 10240 (per-CTA histogram in shared memory)");
         return FPT_EINVAL;
     }
+    void (*kernel)(NoAllocArgs) = d.kind == kUnder     ? noalloc_kernel<kUnder, kEuler>
+                                  : d.kind == kOver      ? noalloc_kernel<kOver, kEuler>
+                                  : d.kind == kUnder + 2 ? noalloc_kernel<kUnder, kHeun>
+                                                         : noalloc_kernel<kOver, kHeun>;
     if (e == cudaSuccess)
-        e = d.model == FPT_UNDERDAMPED
-                ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, noalloc_kernel<kUnder>, kBlock, shmem)
-                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, noalloc_kernel<kOver>, kBlock, shmem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, shmem);
     if (e != cudaSuccess) {
         set_error(std::string("fpt_run_noalloc set-up: ") + cudaGetErrorString(e));
         return FPT_ECUDA;
@@ -370,10 +372,7 @@ extern "C" fpt_status fpt_run_noalloc(const fpt_params *params, uint64_t n_traj,
     a.hist = reinterpret_cast<unsigned long long *>(d_hist);
     a.scratch = scratch;
     a.rec_bytes = rec;
-    if (d.model == FPT_UNDERDAMPED)
-        noalloc_kernel<kUnder><<<grid, kBlock, shmem, s>>>(a);
-    else
-        noalloc_kernel<kOver><<<grid, kBlock, shmem, s>>>(a);
+    kernel<<<grid, kBlock, shmem, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error(std::string("fpt_run_noalloc launch: ") + cudaGetErrorString(e));

@@ -7,6 +7,12 @@
 //   gamma_k = gamma0 + (nu dt) k
 //   underdamped  phi_k = phi + v dt ;  v_k = (v + ((-alpha v - A sin phi) + gamma_k) dt) + sigma z
 //   overdamped   phi_k = (phi + (gamma_k - A sin phi) dt) + sigma z
+// and for the stochastic Heun integrator (gamma_{k-1}, gamma_k at the two ends of the step)
+//   underdamped  a0 = ((-alpha v) - A sin phi) + gamma_{k-1};  p = phi + v dt;
+//                q = (v + a0 dt) + sigma z;  a1 = ((-alpha q) - A sin p) + gamma_k
+//                phi_k = phi + ((v + q) 0.5) dt;  v_k = (v + ((a0 + a1) 0.5) dt) + sigma z
+//   overdamped   f0 = gamma_{k-1} - A sin phi;  p = (phi + f0 dt) + sigma z;  f1 = gamma_k - A sin p
+//                phi_k = (phi + ((f0 + f1) 0.5) dt) + sigma z
 // with an unwrapped phase.  FP32 kernel: the engine's single-precision step on a wrapped phase.
 #include <cstdint>
 #include <cstring>
@@ -22,7 +28,7 @@ namespace {
 __device__ __forceinline__ uint32_t lo32(uint64_t x) { return static_cast<uint32_t>(x); }
 __device__ __forceinline__ uint32_t hi32(uint64_t x) { return static_cast<uint32_t>(x >> 32); }
 
-template <int M>
+template <int M, int H>
 __global__ void __launch_bounds__(128) plain_f64_kernel(PlainArgs a) {
     const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
@@ -42,7 +48,23 @@ __global__ void __launch_bounds__(128) plain_f64_kernel(PlainArgs a) {
             k += 1;
             const double g = __dadd_rn(a.gamma0, __dmul_rn(a.nudt, static_cast<double>(k)));
             const double sn = sin(phi);
-            if constexpr (M == kUnder) {
+            if constexpr (H == kHeun) {
+                const double g0 = __dadd_rn(a.gamma0, __dmul_rn(a.nudt, static_cast<double>(k - 1)));
+                const double nz = __dmul_rn(a.sigma, z[s]);
+                if constexpr (M == kUnder) {
+                    const double a0 = __dadd_rn(__dsub_rn(__dmul_rn(-a.alpha, v), __dmul_rn(a.amp, sn)), g0);
+                    const double p = __dadd_rn(phi, __dmul_rn(v, a.dt));
+                    const double q = __dadd_rn(__dadd_rn(v, __dmul_rn(a0, a.dt)), nz);
+                    const double a1 = __dadd_rn(__dsub_rn(__dmul_rn(-a.alpha, q), __dmul_rn(a.amp, sin(p))), g);
+                    phi = __dadd_rn(phi, __dmul_rn(__dmul_rn(__dadd_rn(v, q), 0.5), a.dt));
+                    v = __dadd_rn(__dadd_rn(v, __dmul_rn(__dmul_rn(__dadd_rn(a0, a1), 0.5), a.dt)), nz);
+                } else {
+                    const double f0 = __dsub_rn(g0, __dmul_rn(a.amp, sn));
+                    const double p = __dadd_rn(__dadd_rn(phi, __dmul_rn(f0, a.dt)), nz);
+                    const double f1 = __dsub_rn(g, __dmul_rn(a.amp, sin(p)));
+                    phi = __dadd_rn(__dadd_rn(phi, __dmul_rn(__dmul_rn(__dadd_rn(f0, f1), 0.5), a.dt)), nz);
+                }
+            } else if constexpr (M == kUnder) {
                 const double phin = __dadd_rn(phi, __dmul_rn(v, a.dt));
                 const double acc = __dadd_rn(__dsub_rn(__dmul_rn(-a.alpha, v), __dmul_rn(a.amp, sn)), g);
                 v = __dadd_rn(__dadd_rn(v, __dmul_rn(acc, a.dt)), __dmul_rn(a.sigma, z[s]));
@@ -64,7 +86,7 @@ done:
 // FP32: wrapped phase r in [-pi, pi) with winding w; escape when r >= eb = phi* - 2 pi w, the
 // threshold in the current cell's coordinates; hb = min(eb, pi) is the one bound tested every
 // step; the lower wrap at -pi is applied at block ends.
-template <int M>
+template <int M, int H>
 __global__ void __launch_bounds__(256) plain_f32_kernel(PlainArgs a) {
     const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
@@ -90,8 +112,8 @@ __global__ void __launch_bounds__(256) plain_f32_kernel(PlainArgs a) {
             const float gs = fmaf(a.nudt_f, Jf, gb);
 #pragma unroll
             for (int s = 0; s < 4; ++s) {
-                step_f32<M>(r, v, rr[s >> 1], tg[s], fmaf(a.nudt_f, static_cast<float>(s + 1), gs),
-                            a.dt_f, a.A_f, a.amp_f);
+                step_f32<M, H>(r, v, rr[s >> 1], tg[s], fmaf(a.nudt_f, static_cast<float>(s), gs),
+                               fmaf(a.nudt_f, static_cast<float>(s + 1), gs), a.dt_f, a.A_f, a.amp_f);
                 if (r >= hb) {
                     // threshold in the current cell: eb = phi* - 2 pi w (same rounding as the engine)
                     const float eb = fmaf(-kTwoPiF, static_cast<float>(w - a.w0), a.eb0_f);
@@ -232,19 +254,25 @@ unsigned grid_for(uint64_t n, unsigned block) {
 
 cudaError_t launch_plain_f64(const PlainArgs &a, cudaStream_t s) {
     const unsigned block = 128;
-    if (a.model == kUnder)
-        plain_f64_kernel<kUnder><<<grid_for(a.n, block), block, 0, s>>>(a);
-    else
-        plain_f64_kernel<kOver><<<grid_for(a.n, block), block, 0, s>>>(a);
+    const unsigned grid = grid_for(a.n, block);
+    switch (a.model + 2 * a.integrator) {
+    case kUnder: plain_f64_kernel<kUnder, kEuler><<<grid, block, 0, s>>>(a); break;
+    case kOver: plain_f64_kernel<kOver, kEuler><<<grid, block, 0, s>>>(a); break;
+    case kUnder + 2: plain_f64_kernel<kUnder, kHeun><<<grid, block, 0, s>>>(a); break;
+    default: plain_f64_kernel<kOver, kHeun><<<grid, block, 0, s>>>(a); break;
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_plain_f32(const PlainArgs &a, cudaStream_t s) {
     const unsigned block = 256;
-    if (a.model == kUnder)
-        plain_f32_kernel<kUnder><<<grid_for(a.n, block), block, 0, s>>>(a);
-    else
-        plain_f32_kernel<kOver><<<grid_for(a.n, block), block, 0, s>>>(a);
+    const unsigned grid = grid_for(a.n, block);
+    switch (a.model + 2 * a.integrator) {
+    case kUnder: plain_f32_kernel<kUnder, kEuler><<<grid, block, 0, s>>>(a); break;
+    case kOver: plain_f32_kernel<kOver, kEuler><<<grid, block, 0, s>>>(a); break;
+    case kUnder + 2: plain_f32_kernel<kUnder, kHeun><<<grid, block, 0, s>>>(a); break;
+    default: plain_f32_kernel<kOver, kHeun><<<grid, block, 0, s>>>(a); break;
+    }
     return cudaGetLastError();
 }
 
@@ -309,6 +337,7 @@ extern "C" fpt_status fpt_plain_launch(const fpt_params *params, uint64_t seed, 
     PlainArgs a;
     std::memset(&a, 0, sizeof(a));
     a.model = d.model;
+    a.integrator = d.integrator;
     a.key0 = static_cast<uint32_t>(seed);
     a.key1 = static_cast<uint32_t>(seed >> 32);
     a.traj0 = traj0;

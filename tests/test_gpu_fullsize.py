@@ -125,3 +125,28 @@ def test_uneven_batch_sampled_requests_invariant(m):
             rid = eng.submit(m.params_from(d, keep_per_traj=1), d["n_traj"], d["seed"])
             eng.wait(rid, 600.0)
             assert (eng.per_traj_steps(rid, d["n_traj"]) == mixed[i]).all()
+
+
+@pytest.mark.parametrize("integrator", ["em", "heun"])
+def test_overdamped_ramp_adiabatic_switching_cdf(m, integrator):
+    """Alg. 3, overdamped, slow ramp (gamma0 = 0.3, nu = 3e-5, D = 0.15, dt = 0.01), 2^18
+    trajectories: the switching-bias CDF agrees with the adiabatic formula from the exact MFPT
+    within 1.5 % everywhere (the agreement the paper reports for Fig. 10b), and the mean within
+    0.5 %."""
+    g0, nu, D, dt, n = 0.3, 3e-5, 0.15, 0.01, 2**18
+    d = workloads.base(model="overdamped", D=D, gamma0=g0, nu=nu, dt=dt, threshold=2 * math.pi,
+                       threshold_mode="from_start", max_steps=int(2.0 / (nu * dt)),
+                       output="bias", integrator=integrator)
+    with m.Engine(0, chunk_steps=16384) as eng:
+        rid = eng.submit(m.params_from(d, keep_per_traj=1), n, 21)
+        res = eng.wait(rid, 600.0)
+        k = eng.per_traj_steps(rid, n)
+    assert res.n_censored == 0 and (k >= 0).all()
+    gs = np.sort(g0 + (nu * dt) * k)
+    grid = np.linspace(g0, 0.95, 651)
+    cdf = mfpt.adiabatic_switching_cdf(grid, g0, nu, D, dt)
+    emp = np.searchsorted(gs, grid, side="right") / n
+    dev = np.max(np.abs(emp - cdf))
+    mean_ad = g0 + np.trapezoid(1.0 - cdf, grid)
+    assert dev < 0.015, dev
+    assert abs(res.mean / mean_ad - 1) < 0.005, (res.mean, mean_ad)

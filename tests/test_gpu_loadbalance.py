@@ -1,6 +1,8 @@
 """App. A on the GPU: a kernel that runs one realisation per thread loses the time its warps and
 CTAs wait for their slowest thread; the persistent engine, which refills lanes, keeps only the
-job-level tail, which App. A's model (list scheduling of the same lengths) predicts.
+job-level tail, which App. A's model (list scheduling of the same lengths at constant speed)
+bounds from below: in the tail, warps that have run dry leave their issue slots to the warps
+still running, which then step faster than in the full machine.
 
 Efficiency is throughput on the noisy problem divided by throughput of the same kernel on a
 noise-free problem where every trajectory has the same length (perfect balance)."""
@@ -55,10 +57,10 @@ def test_plain_kernel_efficiency_follows_appendix_a():
     assert eff_plain < 0.5
     # the engine on the same two problems: its lanes refill the moment they are free, so the
     # only loss left is the job's tail -- App. A with N_tpb = lanes and N_L = n / lanes, i.e.
-    # list scheduling of the very same lengths
+    # list scheduling of the very same lengths, at constant speed a lower bound
     e_noisy, te_noisy, lanes = _timed_engine(m, noisy, n, 3)
     e_bal, te_bal, _ = _timed_engine(m, balanced, n, 3)
     eff_engine = (e_noisy / te_noisy) / (e_bal / te_bal)
     pred = lb.greedy_efficiency(s_noisy, lanes) / lb.greedy_efficiency(s_bal, lanes)
-    assert abs(eff_engine / pred - 1) < 0.15, (eff_engine, pred)
+    assert 0.95 * pred <= eff_engine <= 1.02, (eff_engine, pred)
     assert eff_engine > 1.5 * eff_plain, (eff_engine, eff_plain)

@@ -26,7 +26,8 @@ def base(**kw) -> dict:
     d = dict(model="underdamped", alpha=0.1, D=0.02, gamma0=0.8, nu=0.0, dt=0.005,
              sin_amp=1.0, phi0=NAN, v0=0.0, threshold=math.pi, threshold_mode="absolute",
              max_steps=10**6, output="time", hist_bins=100, hist_lo=0.0, hist_hi=1.0,
-             stop_rse=0.0, stop_block=4096, precision="fp32", n_traj=4096, seed=1)
+             stop_rse=0.0, stop_block=4096, precision="fp32", integrator="em", n_traj=4096,
+             seed=1)
     d.update(kw)
     return d
 
