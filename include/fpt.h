@@ -142,8 +142,8 @@ typedef struct {
     void *stream;               /* cudaStream_t to run on (NULL = engine-owned stream) */
     int32_t threads_per_block;  /* 0 = default (256) */
     int32_t blocks_per_sm;      /* 0 = as many as fit */
-    int32_t traj_per_thread;    /* 1 or 2 (0 = default 2) */
-    uint32_t chunk_steps;       /* steps per resident-kernel launch, multiple of 4 (0 = 16384) */
+    int32_t traj_per_thread;    /* 1 or 2 (0 = default 1) */
+    uint32_t chunk_steps;       /* steps per resident-kernel launch, multiple of 16 (0 = 16384) */
     int32_t service_thread;     /* 1: an engine thread drives the GPU; 0: caller calls fpt_step */
     int32_t use_graph;          /* 1: replay a CUDA graph per iteration (default 1) */
 } fpt_engine_config;
@@ -259,9 +259,12 @@ fpt_status fpt_run_noalloc(const fpt_params *params, uint64_t n_traj, uint64_t s
 fpt_status fpt_philox_fill(uint64_t seed, uint64_t traj, uint64_t block0, uint64_t nblocks,
                            uint32_t *d_out, void *stream);
 
-/* Normals n0 .. n0+n-1 of trajectory `traj` as the integrator draws them (precision FPT_FP64:
- * the oracle's Box-Muller; FPT_FP32: the engine's single-precision map), unit variance, into
- * d_out (device, n doubles). */
+/* Normals n0 .. n0+n-1 of trajectory `traj` as the integrator draws them, unit variance, into
+ * d_out (device, n doubles).  Normal n comes from words (x0,x1) (n mod 4 = 0, 1) or (x2,x3)
+ * (n mod 4 = 2, 3) of Philox block n / 4, cosine first.  FPT_FP64: u = (x + 1/2) 2^-32,
+ * R = sqrt(-2 ln u1), theta = 2 pi u2, each operation rounded.  FPT_FP32: the single-precision
+ * map of the FP32 kernels (u1 rounded to 23 bits, fast log2 / sqrt / sincos, the angle
+ * 2 pi (u2 - 2^-24) - pi with the radius negated: the FP64 pair rotated by 3.7e-7 rad). */
 fpt_status fpt_normals_fill(int precision, uint64_t seed, uint64_t traj, uint64_t n0, uint64_t n,
                             double *d_out, void *stream);
 

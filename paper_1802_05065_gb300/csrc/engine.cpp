@@ -73,7 +73,7 @@ struct CkptHeader {
     uint64_t n_park, has_per_traj;
 };
 constexpr uint64_t kCkptMagic = 0x5450464B43505446ull;   // "FTPCKFPT"
-constexpr uint64_t kCkptVersion = 1;
+constexpr uint64_t kCkptVersion = 2;   // 2: Philox block counts are multiples of kBlockPhilox
 
 // Ring of suspended trajectories: never more than the lanes can hold twice over.
 uint32_t park_capacity(uint64_t n_traj, unsigned lanes) {
@@ -538,11 +538,12 @@ fpt_status create_impl(const fpt_engine_config *cfg_in, fpt_engine *e) {
     if (e->maxr > 1024) return fail(e, FPT_EINVAL, "max_requests must be <= 1024");
     e->block = cfg.threads_per_block > 0 ? cfg.threads_per_block : 256;
     if (e->block % 32 || e->block > 256) return fail(e, FPT_EINVAL, "threads_per_block: multiple of 32, <= 256");
-    e->T = cfg.traj_per_thread > 0 ? cfg.traj_per_thread : 2;
+    e->T = cfg.traj_per_thread > 0 ? cfg.traj_per_thread : 1;
     if (e->T != 1 && e->T != 2) return fail(e, FPT_EINVAL, "traj_per_thread must be 1 or 2");
     const uint32_t chunk = cfg.chunk_steps ? cfg.chunk_steps : 16384;
-    if (chunk % 4 || chunk > (1u << 24)) return fail(e, FPT_EINVAL, "chunk_steps: multiple of 4, <= 2^24");
-    e->chunk_blocks = chunk / 4;
+    if (chunk % kBlockSteps || chunk > (1u << 24))
+        return fail(e, FPT_EINVAL, "chunk_steps: multiple of 16 (the kernel's block), <= 2^24");
+    e->chunk_blocks = chunk / kBlockSteps;
     CK(cudaDeviceGetAttribute(&e->sms, cudaDevAttrMultiProcessorCount, cfg.device));
     int bps = 0;
     CK(engine_chunk_occupancy(e->T, e->block, &bps));
@@ -1012,12 +1013,12 @@ extern "C" fpt_status fpt_get_counters(fpt_engine *e, fpt_engine_counters *out) 
     out->useful_steps = e->h_counters[kCntUseful];
     out->escapes = e->h_counters[kCntEscapes];
     out->censored = e->h_counters[kCntCensored];
-    out->lane_step_slots = e->iterations * static_cast<uint64_t>(e->lanes) * e->chunk_blocks * 4;
+    out->lane_step_slots = e->iterations * static_cast<uint64_t>(e->lanes) * e->chunk_blocks * kBlockSteps;
     out->lanes = e->lanes;
     out->grid = e->grid;
     out->block = e->block;
     out->traj_per_thread = e->T;
-    out->chunk_steps = e->chunk_blocks * 4;
+    out->chunk_steps = e->chunk_blocks * kBlockSteps;
     out->kernel_ms = e->kernel_ms;
     out->preempted = e->preempted;
     for (int s = 0; s < e->maxr; ++s)

@@ -6,7 +6,8 @@
 //                             state and the running sums of the completed id-block prefix
 //   lane state, structure of arrays, one entry per lane (lanes = threads x T):
 //       r (wrapped phase), v, hb (upper event bound), w (winding), c (64-bit Philox block
-//       counter = completed 4-step blocks), gid (64-bit trajectory id), slot, budget
+//       counter = Philox blocks of 4 steps consumed, a multiple of kBlockPhilox between kernel
+//       blocks), gid (64-bit trajectory id), slot, budget
 //   per request: IdBlockAcc[n_idblocks] + u32 histogram rows [n_idblocks][hist_bins]
 //       (+ optional int64 escape step per trajectory)
 #pragma once
@@ -21,7 +22,7 @@ enum : int { kSlotFree = 0, kSlotActive = 1, kSlotFinished = 2, kSlotCancelled =
 // Euler-Maruyama / Heun).  A warp runs one kind at a time.
 constexpr int kNumKinds = 4;
 
-// Blocks (of 4 steps) between re-bases of a trajectory's single-precision bias: gamma_k is
+// Philox blocks (of 4 steps) between re-bases of a trajectory's single-precision bias: gamma_k is
 // formed as gs + nu dt (s + 1) with gs = gb + nu dt Jf and gb = gamma0 + nu dt 4 c_base in FP64,
 // c_base the trajectory's own block count rounded down to a multiple of kRebaseBlocks, so the
 // rounding depends only on the trajectory's step count, never on scheduling.

@@ -1,10 +1,11 @@
 // engine_kernels.cu -- the persistent batched FPT kernel and the completion scan.
 //
-// One launch ("chunk") advances every resident lane by up to chunk_blocks x 4 steps
-// (Euler-Maruyama or stochastic Heun).  A lane integrates one trajectory: Philox4x32-10 ->
-// Box-Muller -> step (Alg. 1 / 3) on a phase wrapped to [-pi, pi) with an integer winding count.  Escape and upper-wrap events
-// are caught by one compare per step (r >= hb); the lower wrap (r < -pi) is applied at the end
-// of each 4-step block.  At the block end the warp votes, finished lanes publish their exact
+// One launch ("chunk") advances every resident lane by up to chunk_blocks blocks of kBlockSteps
+// steps (Euler-Maruyama or stochastic Heun).  A lane integrates one trajectory: Philox4x32-10 ->
+// Box-Muller -> step (Alg. 1 / 3) on a phase wrapped to [-pi, pi) with an integer winding
+// count.  Escape and upper-wrap events are caught by one running maximum per block (exact replay
+// of the rare block that reached a bound); the lower wrap (r < -pi) is applied at the end of
+// each block.  At the block end the warp votes, finished lanes publish their exact
 // result and the warp refills them -- first with suspended trajectories, then with new ids from
 // the requests' work queues (warp-aggregated atomics) -- so lanes never wait for the slowest
 // trajectory of a batch (the dynamic job assignment of Sec. III.B, Fig. 6).
@@ -34,7 +35,7 @@ struct Lane {
     float r, v, hb;
     int w, slot, esc;
     unsigned c_lo, c_hi, gid_lo, gid_hi;
-    unsigned budget;      // blocks to the next event: step budget end or bias re-base
+    unsigned budget;      // blocks to the next event: step budget end, bias re-base, carry
     float gb, Jf;         // bias base and 4 x blocks since the base (exact)
     float dt, A, amp, bmc, nudt;
     unsigned k0, k1;
@@ -78,10 +79,11 @@ __device__ __forceinline__ unsigned long long lane_c(const Lane &L) {
     return (static_cast<unsigned long long>(L.c_hi) << 32) | L.c_lo;
 }
 
-// Bias base and event countdown from the trajectory's block count c:
+// Bias base and event countdown from the trajectory's Philox block count c (4 steps each; c is
+// a multiple of kBlockPhilox at block boundaries):
 // gb = gamma0 + nu dt 4 c_base (FP64, rounded once), Jf = 4 (c - c_base),
-// budget = blocks until the step budget ends, the next re-base or the next carry of the low
-// 32-bit word of c, whichever is first (the high word is only updated at that event).
+// budget = kernel blocks until the step budget ends, the next re-base or the next carry of the
+// low 32-bit word of c, whichever is first (the high word is only updated at that event).
 __device__ __forceinline__ void set_progress(Lane &L, const SlotDev *S) {
     const unsigned long long c = lane_c(L);
     const unsigned long long cb = c - (c % kRebaseBlocks);
@@ -92,7 +94,7 @@ __device__ __forceinline__ void set_progress(Lane &L, const SlotDev *S) {
     const unsigned long long to_carry = 0x100000000ull - (c & 0xFFFFFFFFull);
     unsigned long long m = to_end < to_base ? to_end : to_base;
     m = m < to_carry ? m : to_carry;
-    L.budget = static_cast<unsigned>(m);
+    L.budget = static_cast<unsigned>((m + kBlockPhilox - 1) / kBlockPhilox);
 }
 
 // Start trajectory `idx` of request slot s.
@@ -212,10 +214,10 @@ __device__ __forceinline__ void finish_lanes(Lane (&L)[T], const EngineDev &E, u
         unsigned long long k = 0;
         bool escaped = false;
         if (esc) {
-            k = 4ull * (c - 1) + static_cast<unsigned long long>(L[t].esc) + 1ull;
+            k = 4ull * (c - kBlockPhilox) + static_cast<unsigned long long>(L[t].esc) + 1ull;
             escaped = k <= max_steps;
         }
-        if (escaped) useful -= static_cast<unsigned long long>(3 - L[t].esc);
+        if (escaped) useful -= static_cast<unsigned long long>(kBlockSteps - 1 - L[t].esc);
         else useful -= 4ull * c - max_steps;
         const unsigned long long gid = (static_cast<unsigned long long>(L[t].gid_hi) << 32) | L[t].gid_lo;
         emit(S, gid, escaped, k);
@@ -317,24 +319,29 @@ __device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, int kin
     }
 }
 
-// Integrate blocks of 4 steps with model M and integrator H until the launch's block count is
-// reached or the whole warp has run out of work.  Returns the next block index.
+// Integrate blocks of kBlockSteps steps with model M and integrator H until the launch's block
+// count is reached or the whole warp has run out of work.  Returns the next block index.
 template <int M, int H, int T>
 __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E, unsigned b, int &n_active,
                                unsigned &cursor, unsigned long long &useful, unsigned &n_esc,
                                unsigned &n_cens) {
     const unsigned nb = E.chunk_blocks;
     while (b < nb) {
-        float rr[T][2], tg[T][4], gs[T];
+        // the block's normals: Philox blocks c .. c + kBlockPhilox - 1 (c is a multiple of
+        // kBlockPhilox, so c_lo + h never carries into c_hi)
+        float rr[T][2 * kBlockPhilox], tg[T][kBlockSteps], gs[T];
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-            const uint4 x = philox4x32_10k(make_uint4(L[t].c_lo, L[t].c_hi, L[t].gid_lo, L[t].gid_hi),
-                                           L[t].K);
-            bm_pair_f32(x.x, x.y, L[t].bmc, rr[t][0], tg[t][0], tg[t][1]);
-            bm_pair_f32(x.z, x.w, L[t].bmc, rr[t][1], tg[t][2], tg[t][3]);
+#pragma unroll
+            for (int h = 0; h < kBlockPhilox; ++h) {
+                const uint4 x = philox4x32_10k(
+                    make_uint4(L[t].c_lo + h, L[t].c_hi, L[t].gid_lo, L[t].gid_hi), L[t].K);
+                bm_pair_f32(x.x, x.y, L[t].bmc, rr[t][2 * h], tg[t][4 * h], tg[t][4 * h + 1]);
+                bm_pair_f32(x.z, x.w, L[t].bmc, rr[t][2 * h + 1], tg[t][4 * h + 2], tg[t][4 * h + 3]);
+            }
             gs[t] = fmaf(L[t].nudt, L[t].Jf, L[t].gb);
         }
-        // Four steps without a branch: each lane only tracks the largest phase of the block.
+        // The block's steps without a branch: each lane only tracks the largest phase of the block.
         // In the rare block where it reached the lane's bound hb, the lane's block is replayed
         // (in the warp's event path below) from the saved start state with the event test after
         // every step, so wraps and the escape step are exactly those of a step-by-step test.
@@ -346,7 +353,7 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
             mx[t] = -INFINITY;
         }
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
+        for (int s = 0; s < kBlockSteps; ++s) {
 #pragma unroll
             for (int t = 0; t < T; ++t) {
                 step_f32<M, H>(L[t].r, L[t].v, rr[t][s >> 1], tg[t][s],
@@ -356,12 +363,12 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
                 mx[t] = fmaxf(mx[t], L[t].r);
             }
         }
-        useful += 4ull * static_cast<unsigned>(n_active);
+        useful += static_cast<unsigned long long>(kBlockSteps) * static_cast<unsigned>(n_active);
         bool ev = false;
 #pragma unroll
         for (int t = 0; t < T; ++t) {
-            L[t].c_lo += 1u;
-            L[t].Jf += 4.0f;
+            L[t].c_lo += kBlockPhilox;
+            L[t].Jf += static_cast<float>(kBlockSteps);
             L[t].budget -= 1u;
             // one vote covers every rare case: a bound reached (escape or upper wrap), the
             // countdown (step budget, bias re-base, low-word carry) and the lower wrap
@@ -375,7 +382,7 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
                     L[t].r = r0s[t];
                     L[t].v = v0s[t];
 #pragma unroll
-                    for (int s = 0; s < 4; ++s) {
+                    for (int s = 0; s < kBlockSteps; ++s) {
                         step_f32<M, H>(L[t].r, L[t].v, rr[t][s >> 1], tg[t][s],
                                        fmaf(L[t].nudt, static_cast<float>(s), gs[t]),
                                        fmaf(L[t].nudt, static_cast<float>(s + 1), gs[t]), L[t].dt,

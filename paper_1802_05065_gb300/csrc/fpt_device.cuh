@@ -22,6 +22,7 @@ constexpr uint32_t kPhiloxW0 = 0x9E3779B9u;
 constexpr uint32_t kPhiloxW1 = 0xBB67AE85u;
 
 constexpr float kPiF = 3.14159265358979323846f;
+
 constexpr float kTwoPiF = 6.28318530717958647692f;
 
 // Round keys of Philox4x32-10 for one key: k_r = k + r W (mod 2^32), r = 0..9.  A lane that
@@ -66,26 +67,33 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1
     return c;
 }
 
-// Single-precision uniform in (0, 1) from the high 23 bits m = x >> 9 of a word:
-// u = (m + 1/2) 2^-23, the double-precision uniform (x + 1/2) 2^-32 rounded to 23 bits, so the
-// FP32 and FP64 normals of one trajectory stay close.  (1 + m 2^-23) - (1 - 2^-24) is exact
-// (Sterbenz), so no int->float conversion is needed.
-__device__ __forceinline__ float uniform_f32(uint32_t x) {
-    return __uint_as_float((x >> 9) | 0x3F800000u) - 0.99999994039535522f;
+// 1 + m 2^-23 with m = x >> 9, the high 23 bits of a word, as a float in [1, 2): one funnel
+// shift of (0x7F : x) by 9 places the exponent bits of 1.0 above m.
+__device__ __forceinline__ float mant_f32(uint32_t x) {
+    return __uint_as_float(__funnelshift_r(x, 0x7Fu, 9));
 }
 
-// Box-Muller pair scaled by the step noise: with bmc = -2 ln(2) sigma^2,
-// rr = sigma R = sqrt(bmc * log2(u1)), theta = 2 pi u2; the two noise increments are
-// rr cos theta and rr sin theta.  They are returned as (rr, cos, sin) and the step multiplies
-// them in an explicit fused multiply-add, so the rounding is the same in every kernel (left to
-// the compiler, the product could be contracted differently from kernel to kernel).
-// The radicand is clamped at 0: the fast log2 can return a tiny positive value for u1 near 1.
+// Single-precision uniform in (0, 1): u = (m + 1/2) 2^-23, the double-precision uniform
+// (x + 1/2) 2^-32 rounded to 23 bits, so the FP32 and FP64 normals of one trajectory stay close.
+// (1 + m 2^-23) - (1 - 2^-24) is exact (Sterbenz), so no int->float conversion is needed.
+__device__ __forceinline__ float uniform_f32(uint32_t x) {
+    return mant_f32(x) - 0.99999994039535522f;
+}
+
+// Box-Muller pair scaled by the step noise: with bmc = -2 ln(2) sigma^2 and u1 from x0,
+// R sigma = sqrt(bmc * log2(u1)).  The angle is formed from x1 in one multiply-add as
+// 2 pi (1 + m 2^-23) - 3 pi = 2 pi (u2 - 2^-24) - pi, which lies in [-pi, pi) where the fast
+// sincos is most accurate; the extra half turn is undone by returning the radius negated,
+// rr = -R sigma, so the two noise increments are rr cos and rr sin -- the FP64 pair of the same
+// words rotated by 2 pi 2^-24 (3.7e-7 rad), which leaves the Gaussian law unchanged.  They are
+// returned as (rr, cos, sin) and the step multiplies them in an explicit fused multiply-add, so
+// the rounding is the same in every kernel.  The radicand is taken in absolute value: the fast
+// log2 can return a tiny positive value for u1 near 1.
 __device__ __forceinline__ void bm_pair_f32(uint32_t x0, uint32_t x1, float bmc, float &rr,
                                             float &cs, float &sn) {
     const float u1 = uniform_f32(x0);
-    const float u2 = uniform_f32(x1);
-    rr = sqrtf(fmaxf(__fmul_rn(bmc, __log2f(u1)), 0.0f));
-    __sincosf(__fmul_rn(kTwoPiF, u2), &sn, &cs);
+    rr = -sqrtf(fabsf(__fmul_rn(bmc, __log2f(u1))));
+    __sincosf(fmaf(kTwoPiF, mant_f32(x1), -9.42477796076937972f), &sn, &cs);
 }
 
 // Double-precision uniform in (0, 1): u = (x + 1/2) 2^-32, exact.

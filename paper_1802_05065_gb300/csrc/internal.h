@@ -16,6 +16,12 @@ void set_error(const std::string &msg);
 const std::string &get_error();
 
 constexpr uint64_t kMaxSteps = 1ull << 48;
+// Steps per block of the single-precision kernels: kBlockPhilox Philox calls (4 normals each).
+// A block runs without a branch; the escape test, the lower wrap and the bias re-base act at
+// block granularity (with exact replay of a block in which a bound was reached), so every FP32
+// kernel must use the same block length to agree bit for bit.
+constexpr int kBlockPhilox = 4;
+constexpr int kBlockSteps = 4 * kBlockPhilox;
 constexpr int kMaxBins = 1 << 20;
 
 // A request decoded on the host (the set-up of Alg. 1 / Alg. 3): double constants used

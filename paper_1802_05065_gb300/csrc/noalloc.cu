@@ -115,17 +115,21 @@ __global__ void __launch_bounds__(kBlock) noalloc_kernel(NoAllocArgs a) {
     unsigned long long done = 0, esc = 0, s1lo = 0, s1hi = 0, s2lo = 0, s2hi = 0, under = 0, over = 0;
 
     while (__any_sync(kFullMask, L.active)) {
-        const uint4 x = philox4x32_10(
-            make_uint4(static_cast<unsigned>(L.c), static_cast<unsigned>(L.c >> 32),
-                       static_cast<unsigned>(a.traj_offset + L.idx),
-                       static_cast<unsigned>((a.traj_offset + L.idx) >> 32)),
-            a.key0, a.key1);
-        float rr[2], tg[4];
-        bm_pair_f32(x.x, x.y, a.bmc, rr[0], tg[0], tg[1]);
-        bm_pair_f32(x.z, x.w, a.bmc, rr[1], tg[2], tg[3]);
+        float rr[2 * kBlockPhilox], tg[kBlockSteps];
+#pragma unroll
+        for (int h = 0; h < kBlockPhilox; ++h) {
+            const unsigned long long b = L.c + h;
+            const uint4 x = philox4x32_10(
+                make_uint4(static_cast<unsigned>(b), static_cast<unsigned>(b >> 32),
+                           static_cast<unsigned>(a.traj_offset + L.idx),
+                           static_cast<unsigned>((a.traj_offset + L.idx) >> 32)),
+                a.key0, a.key1);
+            bm_pair_f32(x.x, x.y, a.bmc, rr[2 * h], tg[4 * h], tg[4 * h + 1]);
+            bm_pair_f32(x.z, x.w, a.bmc, rr[2 * h + 1], tg[4 * h + 2], tg[4 * h + 3]);
+        }
         const float gs = fmaf(a.nudt, L.Jf, L.gb);
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
+        for (int s = 0; s < kBlockSteps; ++s) {
             step_f32<M, H>(L.r, L.v, rr[s >> 1], tg[s], fmaf(a.nudt, static_cast<float>(s), gs),
                            fmaf(a.nudt, static_cast<float>(s + 1), gs), a.dt, a.A, a.amp);
             if (L.r >= L.hb) {
@@ -146,8 +150,8 @@ __global__ void __launch_bounds__(kBlock) noalloc_kernel(NoAllocArgs a) {
             L.hb = fminf(fmaf(-kTwoPiF, static_cast<float>(L.w - a.w0), a.eb0), kPiF);
         }
         if (L.active) {
-            L.c += 1;
-            L.Jf += 4.0f;
+            L.c += kBlockPhilox;
+            L.Jf += static_cast<float>(kBlockSteps);
             if ((L.c & ((1ull << 20) - 1)) == 0) {   // re-base the single-precision bias
                 L.gb = static_cast<float>(a.gamma0 + a.nudt_d * static_cast<double>(4ull * L.c));
                 L.Jf = 0.0f;
@@ -157,7 +161,7 @@ __global__ void __launch_bounds__(kBlock) noalloc_kernel(NoAllocArgs a) {
                 unsigned long long k = 0;
                 bool escaped = false;
                 if (L.esc >= 0) {
-                    k = 4ull * (L.c - 1) + static_cast<unsigned long long>(L.esc) + 1ull;
+                    k = 4ull * (L.c - kBlockPhilox) + static_cast<unsigned long long>(L.esc) + 1ull;
                     escaped = k <= a.max_steps;
                 }
                 done += 1;

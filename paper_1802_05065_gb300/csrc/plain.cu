@@ -85,7 +85,8 @@ done:
 
 // FP32: wrapped phase r in [-pi, pi) with winding w; escape when r >= eb = phi* - 2 pi w, the
 // threshold in the current cell's coordinates; hb = min(eb, pi) is the one bound tested every
-// step; the lower wrap at -pi is applied at block ends.
+// step; the lower wrap at -pi is applied at the ends of blocks of kBlockSteps steps, as in the
+// engine.
 template <int M, int H>
 __global__ void __launch_bounds__(256) plain_f32_kernel(PlainArgs a) {
     const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -103,15 +104,19 @@ __global__ void __launch_bounds__(256) plain_f32_kernel(PlainArgs a) {
         const uint64_t seg_end = blk + (1ull << 20) < nblocks ? blk + (1ull << 20) : nblocks;
         const float gb = static_cast<float>(a.gamma0 + a.nudt * static_cast<double>(4 * blk));
         float Jf = 0.0f;
-        for (; blk < seg_end; ++blk) {
-            const uint4 x = philox4x32_10(make_uint4(lo32(blk), hi32(blk), lo32(gid), hi32(gid)),
-                                          a.key0, a.key1);
-            float rr[2], tg[4];
-            bm_pair_f32(x.x, x.y, a.bmc_f, rr[0], tg[0], tg[1]);
-            bm_pair_f32(x.z, x.w, a.bmc_f, rr[1], tg[2], tg[3]);
+        for (; blk < seg_end; blk += kBlockPhilox) {
+            float rr[2 * kBlockPhilox], tg[kBlockSteps];
+#pragma unroll
+            for (int h = 0; h < kBlockPhilox; ++h) {
+                const uint64_t b = blk + h;
+                const uint4 x = philox4x32_10(make_uint4(lo32(b), hi32(b), lo32(gid), hi32(gid)),
+                                              a.key0, a.key1);
+                bm_pair_f32(x.x, x.y, a.bmc_f, rr[2 * h], tg[4 * h], tg[4 * h + 1]);
+                bm_pair_f32(x.z, x.w, a.bmc_f, rr[2 * h + 1], tg[4 * h + 2], tg[4 * h + 3]);
+            }
             const float gs = fmaf(a.nudt_f, Jf, gb);
 #pragma unroll
-            for (int s = 0; s < 4; ++s) {
+            for (int s = 0; s < kBlockSteps; ++s) {
                 step_f32<M, H>(r, v, rr[s >> 1], tg[s], fmaf(a.nudt_f, static_cast<float>(s), gs),
                                fmaf(a.nudt_f, static_cast<float>(s + 1), gs), a.dt_f, a.A_f, a.amp_f);
                 if (r >= hb) {
@@ -132,7 +137,7 @@ __global__ void __launch_bounds__(256) plain_f32_kernel(PlainArgs a) {
                 w -= 1;
                 hb = fminf(fmaf(-kTwoPiF, static_cast<float>(w - a.w0), a.eb0_f), kPiF);
             }
-            Jf += 4.0f;
+            Jf += static_cast<float>(kBlockSteps);
         }
     }
 done:

@@ -8,8 +8,9 @@
 * All four kinds (model x integrator) in one engine: each request identical to its plain run.
 * A never-ending Heun request does not starve an Euler request (warps of one kind vacate).
 * The allocation-free entry point gives the engine's result for a Heun request.
-* Large step: at dt = 0.05 the Heun mean escape time of the overdamped point gamma = 0.9,
-  D = 0.2 equals the exact MFPT plus the monitoring delay, where Euler's first-order bias shows.
+* Step-size convergence: overdamped, the Heun mean approaches the exact MFPT plus the monitoring
+  delay as dt shrinks (0.2 -> 0.05); underdamped, the Heun mean does not move between dt = 0.1
+  and 0.025 while Euler's is > 20 % short at dt = 0.025.
 """
 import math
 
@@ -139,17 +140,42 @@ def test_noalloc_heun_matches_engine(m, api):
     assert (steps.cpu().numpy() == ref).all()
 
 
-def test_heun_large_step_vs_exact_mfpt(m):
-    g, D, dt, n = 0.9, 0.2, 0.05, 2**20
-    want = mfpt.overdamped_mfpt(g, D) + mfpt.monitoring_shift(g, D, dt)
-    out = {}
-    for integ in ("heun", "em"):
-        d = workloads.scaled(OVER, dt=dt, integrator=integ)
-        with m.Engine(0, chunk_steps=4096) as eng:
-            res = eng.wait(eng.submit(m.params_from(d), n, 11), 600.0)
-        assert res.n_used == n and res.n_censored == 0
-        out[integ] = (res.mean, res.sem)
-    hm, hs = out["heun"]
-    em, es = out["em"]
-    assert abs(hm - want) < 3.5 * hs + 0.002 * want, (out, want)
-    assert abs(em - want) > 3 * abs(hm - want), (out, want)
+def _means(m, reqs, n, seed):
+    with m.Engine(0, chunk_steps=16384) as eng:
+        ids = [eng.submit(m.params_from(d), n, seed) for d in reqs]
+        out = [eng.wait(r, 900.0) for r in ids]
+    for r in out:
+        assert r.n_used == n and r.n_censored == 0
+    return [(r.mean, r.sem) for r in out]
+
+
+def test_heun_overdamped_dt_convergence_to_quadrature(m):
+    """gamma = 0.9, D = 0.2, 2^22 trajectories, dt = 0.2, 0.1, 0.05 (200, 100, 50 times the
+    sweep's step): the Heun mean minus (exact MFPT + monitoring delay) shrinks with dt, about
+    halving from dt = 0.2 to 0.1 (the next order of the once-per-step level test, 0.9 % and
+    0.4 % of T), and is within 0.25 % of T at dt = 0.05."""
+    g, D, n = 0.9, 0.2, 2**22
+    T = mfpt.overdamped_mfpt(g, D)
+    dts = (0.2, 0.1, 0.05)
+    res = _means(m, [workloads.scaled(OVER, dt=dt) for dt in dts], n, 11)
+    err = [mu - T - mfpt.monitoring_shift(g, D, dt) for (mu, _), dt in zip(res, dts)]
+    se = res[-1][1]
+    assert err[0] > err[1] > err[2] - 2 * se and err[2] > -3 * se, err
+    assert 1.5 < err[0] / err[1] < 3.0, err
+    assert abs(err[2]) < 3.5 * se + 0.0025 * T, (err, se)
+
+
+def test_heun_underdamped_step_independence_where_euler_drifts(m):
+    """Underdamped, alpha = 0.1, gamma = 0.8, D = 0.05, 2^18 trajectories.  Heun's mean escape
+    time is the same at dt = 0.1 and dt = 0.025 (within 3.5 combined SE); Euler's first-order
+    energy gain (the explicit update of an oscillator multiplies its energy by 1 + w^2 dt^2 per
+    step, which heats the junction) makes its mean at dt = 0.025 more than 20 % short, and the
+    shortfall shrinks when dt is halved."""
+    base = workloads.scaled(UNDER, max_steps=10**9)
+    reqs = [workloads.scaled(base, dt=0.1), workloads.scaled(base, dt=0.025),
+            workloads.scaled(base, dt=0.025, integrator="em"),
+            workloads.scaled(base, dt=0.0125, integrator="em")]
+    (h1, s1), (h2, s2), (e1, _), (e2, _) = _means(m, reqs, 2**18, 13)
+    assert abs(h1 - h2) < 3.5 * math.hypot(s1, s2), (h1, s1, h2, s2)
+    assert e1 < 0.8 * h2, (e1, h2)
+    assert e1 < e2 < h2, (e1, e2, h2)
