@@ -44,7 +44,7 @@ WORKLOAD = ("overdamped tilted washboard sweep: gamma {0.3,0.5,0.7,0.9} x D {0.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--chunk-steps", type=int, default=65536)
@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-heun", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="use --traj-per-thread / --block as given instead of the autotuner's choice")
     ap.add_argument("--serving-requests", type=int, default=100)
     return ap.parse_args()
 
@@ -92,7 +94,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
-                 "-i", str(self.index), "-lms", "200"],
+                 "-i", str(self.index), "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -100,9 +102,15 @@ class ClockSampler:
             self.proc = None
         return self
 
+    def wait_first(self, timeout: float):
+        """Block until the first sample has arrived (nvidia-smi takes a moment to start)."""
+        end = time.perf_counter() + timeout
+        while self.proc and not self.lines and time.perf_counter() < end:
+            time.sleep(0.01)
+
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
     def __exit__(self, *a):
         if self.proc:
@@ -114,10 +122,14 @@ class ClockSampler:
             if self.t:
                 self.t.join(timeout=2)
 
-    def summary(self):
+    def summary(self, t0=None, t1=None):
+        """Median SM clock and the throttle reasons seen in samples taken between t0 and t1
+        (perf_counter seconds; the whole run when not given)."""
         sm, mx, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        for ts, ln in self.lines:
+            if (t0 is not None and ts < t0) or (t1 is not None and ts > t1):
+                continue
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue
@@ -261,11 +273,24 @@ def run_ours(args):
 
     n_traj = 2**20
     pts = workloads.overdamped_sweep(n_traj=n_traj)
+    # launch shape (trajectories per thread, threads per block) from the autotuner, measured on a
+    # short run of the same sweep; the chunk stays the bench's step (--chunk-steps)
+    tuned = None
+    if not args.no_autotune:
+        from paper_1802_05065_gb300 import autotune
+        tuned = autotune.tune([(d, 2**18, d["seed"]) for d in pts], device=local, iters=3,
+                              chunk=8192, save=False)
+        args.traj_per_thread = tuned["best"]["traj_per_thread"]
+        args.block = tuned["best"]["threads_per_block"]
     eng = pkg.Engine(local, chunk_steps=args.chunk_steps, traj_per_thread=args.traj_per_thread,
                      threads_per_block=args.block)
     stream = torch.cuda.ExternalStream(eng.stream, device=torch.device("cuda", local))
     rids = [eng.submit(pkg.params_from(d, traj_offset=rank * n_traj), n_traj, d["seed"])
             for d in pts]
+    # the clock sampler runs from before the warm-up; only its samples inside the timed region
+    # are summarised
+    clk = ClockSampler(local).__enter__()
+    clk.wait_first(3.0)
     for _ in range(args.warmup):
         eng.step(1)
     flush = None if args.no_flush else torch.empty(512 * 2**20, dtype=torch.uint8,
@@ -276,15 +301,17 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clk:
-        for i in range(args.steps):
-            if flush is not None:
-                with torch.cuda.stream(stream):
-                    flush.fill_(i & 0xFF)
-            evs[i][0].record(stream)
-            eng.step(1)
-            evs[i][1].record(stream)
-        torch.cuda.synchronize()
+    t_timed0 = time.perf_counter()
+    for i in range(args.steps):
+        if flush is not None:
+            with torch.cuda.stream(stream):
+                flush.fill_(i & 0xFF)
+        evs[i][0].record(stream)
+        eng.step(1)
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    t_timed1 = time.perf_counter()
+    clk.__exit__(None, None, None)
     barrier()
     torch.cuda.synchronize()
     c1 = eng.counters()
@@ -435,7 +462,7 @@ def run_ours(args):
     n_sm = props.multi_processor_count
     peaks = measured_peaks()
     f_max = float(peaks.get("sm_max_mhz", 2070.0))
-    clocks = clk.summary()
+    clocks = clk.summary(t_timed0, t_timed1)
     peak, xu_step, xu_rate = roofline_model(n_sm, f_max)
     per_gpu_steps_s = steps / (ms / 1e3)
     kern_steps_s = steps / (kernel_ms / 1e3) if kernel_ms > 0 else None
@@ -463,6 +490,7 @@ def run_ours(args):
                    "step": f"one engine iteration: {args.chunk_steps} steps per lane",
                    "lanes": c1["lanes"], "grid": c1["grid"], "block": c1["block"],
                    "traj_per_thread": c1["traj_per_thread"],
+                   "launch_shape": "autotuned" if tuned else "fixed",
                    "l2": "flushed between timed iterations (512 MiB write)" if flush is not None
                    else "not flushed", "parallelism": f"replicas x{world}"},
         "escapes_per_s": esc_all / (ms_max / 1e3),
@@ -475,6 +503,10 @@ def run_ours(args):
         "fp64_plain": fp64,
         "fp32_engine_point": fast_point,
         "heun": heun,
+        "autotune": None if not tuned else {
+            "best": tuned["best"], "chunk_for_2pct_overhead": tuned["chunk_steps"],
+            "trials": [{"cfg": t["cfg"], "gstep_s": round(t["steps_per_s_kernel"] / 1e9, 1)}
+                       for t in tuned["trials"]]},
         "serving": serving,
         "gpu_launches": 2 * args.steps,   # chunk + scan per timed iteration
         "clocks": clocks,
