@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-heun", action="store_true")
+    ap.add_argument("--no-mix", action="store_true",
+                    help="skip the ramp-sweep and uneven-batch throughput legs")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use --traj-per-thread / --block as given instead of the autotuner's choice")
     ap.add_argument("--serving-requests", type=int, default=100)
@@ -435,6 +437,46 @@ def run_ours(args):
                 "xu_ops_per_step": 4.0, "integrator": "stochastic Heun, same sweep"}
         eng3.close()
 
+    # throughput on the other two batch workloads, a few engine iterations each: the ramp sweep
+    # (Alg. 3, 4 rates x 2^20 trajectories) and the 256-set uneven batch (2^12..2^18
+    # trajectories per set, constant and ramped, lengths 10^3..10^8 steps) in one engine
+    def _leg(reqs, iters, chunk):
+        e4 = pkg.Engine(local, chunk_steps=chunk, traj_per_thread=args.traj_per_thread,
+                        threads_per_block=args.block)
+        s4 = torch.cuda.ExternalStream(e4.stream, device=torch.device("cuda", local))
+        for d, n, sd in reqs:
+            e4.submit(pkg.params_from(d), n, sd)
+        e4.step(2)
+        a0 = e4.counters()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(iters)]
+        torch.cuda.synchronize()
+        for i in range(iters):
+            ev[i][0].record(s4)
+            e4.step(1)
+            ev[i][1].record(s4)
+        torch.cuda.synchronize()
+        a1 = e4.counters()
+        e4.close()
+        ms4 = sum(x.elapsed_time(y) for x, y in ev)
+        st4 = a1["useful_steps"] - a0["useful_steps"]
+        km4 = a1["kernel_ms"] - a0["kernel_ms"]
+        slots4 = a1["lane_step_slots"] - a0["lane_step_slots"]
+        return {"value": st4 / (ms4 / 1e3), "unit": UNIT, "iterations": iters,
+                "steps_per_iteration": chunk,
+                "kernel_gstep_s": st4 / (km4 / 1e3) / 1e9 if km4 > 0 else None,
+                "warp_active_fraction": st4 / slots4 if slots4 else None,
+                "escapes_per_s": (a1["escapes"] - a0["escapes"]) / (ms4 / 1e3)}
+    mix = None
+    if not args.no_mix and rank == 0:
+        ramp = [(d, n_traj, d["seed"]) for d in workloads.ramp_sweep(n_traj=n_traj)]
+        ub = [(d, d["n_traj"], d["seed"]) for d in workloads.uneven_batch()]
+        mix = {"ramp_sweep": _leg(ramp, 5, 65536),
+               "uneven_batch": _leg(ub, 10, 16384)}
+        mix["ramp_sweep"]["workload"] = "ramp sweep nu {1e-5..1e-8}, 4 x 2^20 trajectories"
+        mix["uneven_batch"]["workload"] = ("uneven batch, 256 sets, 2^12..2^18 trajectories, "
+                                           "half ramped, one engine")
+
     serving = None
     if not args.no_serving and rank == 0 and world == 1:
         from paper_1802_05065_gb300 import serving as _srv
@@ -503,6 +545,7 @@ def run_ours(args):
         "fp64_plain": fp64,
         "fp32_engine_point": fast_point,
         "heun": heun,
+        "other_workloads": mix,
         "autotune": None if not tuned else {
             "best": tuned["best"], "chunk_for_2pct_overhead": tuned["chunk_steps"],
             "trials": [{"cfg": t["cfg"], "gstep_s": round(t["steps_per_s_kernel"] / 1e9, 1)}

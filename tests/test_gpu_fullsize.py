@@ -150,3 +150,25 @@ def test_overdamped_ramp_adiabatic_switching_cdf(m, integrator):
     mean_ad = g0 + np.trapezoid(1.0 - cdf, grid)
     assert dev < 0.015, dev
     assert abs(res.mean / mean_ad - 1) < 0.005, (res.mean, mean_ad)
+
+
+def test_li07_device_ramp_vs_oracle(m):
+    """The Fig. 10b junction (R 250 ohm, C 88 fF, Ic 0.748 uA, T 1.2 K) in engine units, with the
+    ramp sped up 10^4-fold (2.8e7 steps to the critical current instead of 2.8e11): the FP32
+    engine's switching-bias mean and distribution (2^14 trajectories) agree with 64 oracle
+    trajectories of independent seeds."""
+    base = workloads.li07_switching()
+    nu = base["nu"] * 1e4
+    d = workloads.scaled(base, nu=nu, max_steps=int(math.ceil(1.1 / (nu * base["dt"]))))
+    n = 2**14
+    with m.Engine(0, chunk_steps=65536) as eng:
+        rid = eng.submit(m.params_from(d, keep_per_traj=1), n, d["seed"])
+        res = eng.wait(rid, 900.0)
+        g = eng.per_traj_steps(rid, n)
+    p = oracle.params_from(d)
+    r = oracle.run(p, d["seed"] + 1, 64)
+    sr = stats.summarize(p, r)
+    assert res.n_censored == 0 and sr.n_censored == 0
+    assert 0.5 < res.mean < 1.0
+    assert stats.within_combined_se(res.mean, res.sem, sr.mean, sr.sem, 3.0)
+    assert stats.ks_pvalue(stats.observables(p, g), stats.observables(p, r)) > 0.01
