@@ -170,3 +170,33 @@ def adiabatic_switching_cdf(gammas, gamma0: float, nu: float, D: float, dt: floa
     rate = 1.0 / (nu * T)
     H = np.concatenate([[0.0], np.cumsum(0.5 * (rate[1:] + rate[:-1]) * np.diff(g))])
     return -np.expm1(-H)
+
+
+def underdamped_rate_bhl(gamma: float, alpha: float, D: float) -> float:
+    """Thermal escape rate of the underdamped junction (plasma-frequency units) in the
+    Buttiker-Harris-Landauer interpolation between energy-diffusion and moderate damping, the
+    rate used with the adiabatic formula for switching-current distributions (Fulton and
+    Dunkleberger; the comparison of Sec. IV.B):
+
+        Gamma = a_t (omega_a / 2 pi) exp(-dU / D),
+        a_t = 4 / (sqrt(1 + Q D / (1.8 dU)) + 1)^2,   Q = omega_a / alpha,
+
+    omega_a = (1 - gamma^2)^(1/4) the small-oscillation frequency at the well bottom and
+    dU = 2 (sqrt(1 - gamma^2) - gamma arccos gamma) the barrier.  An interpolation: expect a few
+    per cent in the rate."""
+    wa = (1.0 - gamma * gamma) ** 0.25
+    dU = barrier(gamma)
+    Q = wa / alpha
+    at = 4.0 / (math.sqrt(1.0 + Q * D / (1.8 * dU)) + 1.0) ** 2
+    return at * wa / (2.0 * math.pi) * math.exp(-dU / D)
+
+
+def adiabatic_switching_cdf_rate(gammas, gamma0: float, nu: float, rate) -> np.ndarray:
+    """P(gamma_sw <= g) = 1 - exp(-(1/nu) Int_{gamma0}^{g} rate(g') dg') for a rate function of
+    the bias (trapezoid rule on the increasing grid `gammas`, which starts at gamma0)."""
+    g = np.asarray(gammas, dtype=np.float64)
+    if g[0] != gamma0 or np.any(np.diff(g) <= 0):
+        raise ValueError("grid must start at gamma0 and increase")
+    r = np.array([rate(x) for x in g]) / nu
+    H = np.concatenate([[0.0], np.cumsum(0.5 * (r[1:] + r[:-1]) * np.diff(g))])
+    return -np.expm1(-H)

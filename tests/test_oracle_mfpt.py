@@ -97,3 +97,25 @@ def test_monitoring_constant():
     """beta = -zeta(1/2)/sqrt(2 pi) = 0.5826 (Broadie-Glasserman-Kou)."""
     assert abs(mfpt.monitoring_shift(0.9, 0.2, 1e-3) /
                (math.sqrt(2 * 0.2 * 1e-3) * mfpt.threshold_sensitivity(0.9, 0.2)) - 0.5826) < 1e-4
+
+
+def test_bhl_rate_limits():
+    """The interpolated underdamped rate reduces to transition-state theory
+    (omega_a / 2 pi) exp(-dU / D) when Q D / dU -> 0, and to Kramers' energy-diffusion rate
+    alpha (36/5) (dU / (omega_a D)) (omega_a / 2 pi) exp(-dU / D) (barrier action of the cubic
+    well 36 dU / (5 omega_a)) when Q D / dU -> infinity."""
+    g, D = 0.6, 0.05
+    wa = (1 - g * g) ** 0.25
+    dU = mfpt.barrier(g)
+    tst = wa / (2 * math.pi) * math.exp(-dU / D)
+    assert abs(mfpt.underdamped_rate_bhl(g, 1e6, D) / tst - 1) < 1e-4
+    alpha = 1e-10   # a_t = 4/(sqrt(1+x)+1)^2 -> 4/x (1 - 2/sqrt(x)): x ~ 1e9 here
+    ed = alpha * (36 / 5) * (dU / (wa * D)) * tst
+    assert abs(mfpt.underdamped_rate_bhl(g, alpha, D) / ed - 1) < 1e-3
+
+
+def test_adiabatic_cdf_of_a_constant_rate_is_exponential():
+    """A bias-independent rate r gives P(gamma_sw <= g) = 1 - exp(-r (g - gamma0) / nu)."""
+    g = np.linspace(0.2, 0.9, 301)
+    c = mfpt.adiabatic_switching_cdf_rate(g, 0.2, 1e-3, lambda x: 0.01)
+    np.testing.assert_allclose(c, -np.expm1(-0.01 * (g - 0.2) / 1e-3), rtol=1e-12, atol=1e-15)
