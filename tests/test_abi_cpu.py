@@ -84,12 +84,14 @@ def test_sums_finish_large_steps(lib):
                                  dict(max_steps=2**49), dict(hist_bins=0),
                                  dict(hist_lo=2.0, hist_hi=1.0), dict(gamma0=1.5),
                                  dict(threshold=0.1), dict(alpha=float("nan")),
-                                 dict(model="nonsense")])
+                                 dict(model="nonsense"), dict(integrator="nonsense")])
 def test_invalid_params_rejected(lib, bad):
     d = workloads.plain_constant_tilt()
-    p = lib.params_from(d, **{k: v for k, v in bad.items() if k != "model"})
+    p = lib.params_from(d, **{k: v for k, v in bad.items() if k not in ("model", "integrator")})
     if "model" in bad:
         p.model = 7
+    if "integrator" in bad:
+        p.integrator = 2
     with pytest.raises(lib.FptError) as ei:
         lib.plain_launch(p, 1, 0, 16, 0, 0)
     assert ei.value.status == -1
