@@ -15,9 +15,10 @@ from . import _lib
 
 
 def run_stream(stream, device: int = 0, chunk_steps: int = 4096, timeout_s: float = 600.0,
-               engine_kw=None):
+               engine_kw=None, keep_results: bool = False):
     """Submit (arrival_time_s, params dict) pairs at their arrival times and wait for all.
-    Returns a dict with latency percentiles and throughput."""
+    Returns a dict with latency percentiles and throughput (and, with keep_results, every
+    request's fpt_result in submission order, None where it did not complete)."""
     kw = dict(engine_kw or {})
     kw.setdefault("chunk_steps", chunk_steps)
     eng = _lib.Engine(device, service_thread=1, **kw)
@@ -46,7 +47,7 @@ def run_stream(stream, device: int = 0, chunk_steps: int = 4096, timeout_s: floa
     finally:
         eng.close()
     lat = np.array(lat) if lat else np.array([float("nan")])
-    return {
+    out = {
         "requests": len(ids), "completed": int(sum(r is not None for r in res)),
         "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
         "mean_s": float(np.mean(lat)), "wall_s": wall, "submit_span_s": t_submitted,
@@ -54,3 +55,6 @@ def run_stream(stream, device: int = 0, chunk_steps: int = 4096, timeout_s: floa
         "trajectories_used": int(sum(r.n_used for r in res if r is not None)),
         "chunk_steps": c["chunk_steps"],
     }
+    if keep_results:
+        out["results"] = res
+    return out
