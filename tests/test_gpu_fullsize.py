@@ -198,3 +198,15 @@ def test_li07_switching_cdf_vs_adiabatic_bhl(m, speedup, n):
     mean_ad = float(np.trapezoid(1.0 - cdf, grid))
     assert dev < 0.04, dev
     assert abs(res.mean / mean_ad - 1) < 0.01, (res.mean, mean_ad)
+
+
+def test_ramp_1e6_long_trajectories_vs_oracle(m):
+    """Alg. 3 at nu = 1e-6 (1.1e8 steps to gamma = 1.1; the single-precision bias is re-based
+    ~20 times per trajectory): 2^16 engine trajectories vs 48 oracle trajectories."""
+    d = workloads.ramp_sweep(rates=(1e-6,))[0]
+    [r] = _engine_run(m, [(d, 2**16, d["seed"])])
+    assert r.n_used == 2**16 and r.n_censored == 0
+    p = oracle.params_from(d)
+    ref = stats.summarize(p, oracle.run(p, d["seed"] + 11, 48))
+    assert ref.n_censored == 0
+    assert stats.within_combined_se(r.mean, r.sem, ref.mean, ref.sem, 3.0)
