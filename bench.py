@@ -403,6 +403,17 @@ def run_ours(args):
         ms32 = a.elapsed_time(b)
         res32, _, _ = api.reduce(d32, st)
         fp64["fp32_plain_value"] = res32.steps_total / (ms32 / 1e3)
+        # the FP64 pipe of this GPU for context: a library DGEMM (cuBLAS) on 8192^2 operands
+        x = torch.randn(8192, 8192, dtype=torch.float64, device=torch.device("cuda", local))
+        torch.matmul(x, x)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(3):
+            torch.matmul(x, x)
+        b.record()
+        torch.cuda.synchronize()
+        fp64["dgemm_tflops"] = 3 * 2 * 8192.0 ** 3 / (a.elapsed_time(b) / 1e3) / 1e12
+        del x
 
     # the same sweep with the stochastic Heun integrator (4 XU evaluations per step: two sin of
     # the predictor-corrector, half of the Box-Muller pair), a few engine iterations
