@@ -963,6 +963,18 @@ extern "C" fpt_status fpt_restore(fpt_engine *e, const void *buf, size_t size, u
     CkptHeader H;
     std::memcpy(&H, buf, sizeof(H));
     if (H.magic != kCkptMagic || H.version != kCkptVersion) return fail(e, FPT_EINVAL, "not a checkpoint");
+    // the header's sizes must be those a request of these parameters has, before any of them
+    // is used to size a copy
+    {
+        Decoded d;
+        std::string err;
+        if (!decode(&H.params, &d, &err)) return fail(e, FPT_EINVAL, "checkpoint parameters: " + err);
+    }
+    const uint32_t B = H.params.stop_block ? H.params.stop_block : 4096;
+    if (H.n_traj < 1 || H.n_traj > (1ull << 40) || H.stop_block != B ||
+        H.n_idblocks != (H.n_traj + B - 1) / B || H.n_park > H.n_traj || H.has_per_traj > 1 ||
+        H.has_per_traj != static_cast<uint64_t>(H.params.keep_per_traj != 0))
+        return fail(e, FPT_EINVAL, "checkpoint header is inconsistent");
     const size_t nb = H.n_idblocks;
     const size_t want = sizeof(CkptHeader) + sizeof(SlotCtl) + nb * sizeof(IdBlockAcc) +
                         nb * static_cast<size_t>(H.params.hist_bins) * 4 +

@@ -317,3 +317,45 @@ def test_checkpoint_of_queued_request(lib, api):
         eng.wait(rid, 600.0)
         steps = eng.per_traj_steps(rid, 3000)
     assert (steps == api.run_plain(CONST_OVER, 3000, 9).cpu().numpy()).all()
+
+
+def test_admission_by_memory_budget(lib, api):
+    """An engine whose device-memory budget holds one such request at a time queues the others
+    (admitted as memory frees), finishes all of them with their exact results, and rejects a
+    request that could never fit."""
+    d = workloads.scaled(CONST_OVER, max_steps=10**8)
+    n = 2**20                                  # keep_per_traj: 8 MB of per-trajectory steps
+    with _engine(lib, chunk_steps=16384, mem_budget_bytes=22 << 20) as eng:
+        ids = [eng.submit(lib_params(d, keep_per_traj=1), n, 40 + i) for i in range(3)]
+        eng.step(1)
+        c = eng.counters()
+        assert c["resident_requests"] == 1 and c["pending_requests"] == 2
+        got = []
+        for rid in ids:
+            eng.wait(rid, 600.0)
+            got.append(eng.per_traj_steps(rid, n))
+            eng.release(rid)
+        with pytest.raises(lib.FptError) as ei:
+            eng.submit(lib_params(d, keep_per_traj=1), 2**23, 1)
+        assert ei.value.status == -2          # FPT_ENOMEM
+    for i, g in enumerate(got):
+        assert (g == api.run_plain(d, n, 40 + i).cpu().numpy()).all()
+
+
+def test_restore_rejects_foreign_or_truncated_blobs(lib):
+    """fpt_restore checks the blob: a wrong magic, another format version or a truncated buffer
+    is rejected with FPT_EINVAL and leaves the engine usable."""
+    import struct
+    with _engine(lib, chunk_steps=2048) as eng:
+        rid = eng.submit(lib_params(CONST_OVER), 4000, 3)
+        eng.step(1)
+        blob = eng.checkpoint(rid)
+        magic, version = struct.unpack_from("<QQ", blob, 0)
+        for bad in (struct.pack("<QQ", magic ^ 1, version) + blob[16:],
+                    struct.pack("<QQ", magic, version + 1) + blob[16:],
+                    blob[: len(blob) // 2]):
+            with pytest.raises(lib.FptError) as ei:
+                eng.restore(bad)
+            assert ei.value.status == -1
+        res = eng.wait(eng.restore(blob), 600.0)
+        assert res.n_used == 4000
