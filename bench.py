@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--chunk-steps", type=int, default=65536)
     ap.add_argument("--traj-per-thread", type=int, default=1)
-    ap.add_argument("--block", type=int, default=256)
+    ap.add_argument("--block", type=int, default=512)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")

@@ -329,7 +329,7 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
     while (b < nb) {
         // the block's normals: Philox blocks c .. c + kBlockPhilox - 1 (c is a multiple of
         // kBlockPhilox, so c_lo + h never carries into c_hi)
-        float rr[T][2 * kBlockPhilox], tg[T][kBlockSteps], gs[T];
+        float rr[T][2 * kBlockPhilox], tg[T][kBlockSteps], gs[T], gsl[T];
 #pragma unroll
         for (int t = 0; t < T; ++t) {
 #pragma unroll
@@ -339,7 +339,7 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
                 bm_pair_f32(x.x, x.y, L[t].bmc, rr[t][2 * h], tg[t][4 * h], tg[t][4 * h + 1]);
                 bm_pair_f32(x.z, x.w, L[t].bmc, rr[t][2 * h + 1], tg[t][4 * h + 2], tg[t][4 * h + 3]);
             }
-            gs[t] = fmaf(L[t].nudt, L[t].Jf, L[t].gb);
+            bias_line<M, H>(fmaf(L[t].nudt, L[t].Jf, L[t].gb), L[t].nudt, L[t].dt, gs[t], gsl[t]);
         }
         // The block's steps without a branch: each lane only tracks the largest phase of the block.
         // In the rare block where it reached the lane's bound hb, the lane's block is replayed
@@ -357,8 +357,8 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
 #pragma unroll
             for (int t = 0; t < T; ++t) {
                 step_f32<M, H>(L[t].r, L[t].v, rr[t][s >> 1], tg[t][s],
-                               fmaf(L[t].nudt, static_cast<float>(s), gs[t]),
-                               fmaf(L[t].nudt, static_cast<float>(s + 1), gs[t]), L[t].dt, L[t].A,
+                               fmaf(gsl[t], static_cast<float>(s), gs[t]),
+                               fmaf(gsl[t], static_cast<float>(s + 1), gs[t]), L[t].dt, L[t].A,
                                L[t].amp);
                 mx[t] = fmaxf(mx[t], L[t].r);
             }
@@ -384,8 +384,8 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
 #pragma unroll
                     for (int s = 0; s < kBlockSteps; ++s) {
                         step_f32<M, H>(L[t].r, L[t].v, rr[t][s >> 1], tg[t][s],
-                                       fmaf(L[t].nudt, static_cast<float>(s), gs[t]),
-                                       fmaf(L[t].nudt, static_cast<float>(s + 1), gs[t]), L[t].dt,
+                                       fmaf(gsl[t], static_cast<float>(s), gs[t]),
+                                       fmaf(gsl[t], static_cast<float>(s + 1), gs[t]), L[t].dt,
                                        L[t].A, L[t].amp);
                         if (L[t].r >= L[t].hb) phase_event(L[t], E, s);
                     }
@@ -401,8 +401,10 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
     return b;
 }
 
+// One trajectory per thread runs best as one CTA of 512 threads per SM (128 registers, 16 warps);
+// two per thread as CTAs of up to 256.
 template <int T>
-__global__ void __launch_bounds__(256) engine_chunk_kernel(EngineDev E) {
+__global__ void __launch_bounds__(T == 1 ? 512 : 256, 1) engine_chunk_kernel(EngineDev E) {
     const unsigned nthreads = gridDim.x * blockDim.x;
     const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned warp = gtid >> 5;

@@ -124,11 +124,27 @@ struct StepConstF32 {
 enum : int { kUnder = 0, kOver = 1 };
 enum : int { kEuler = 0, kHeun = 1 };
 
-// One step with noise increment sigma z = rr * trig; g0 = gamma_{k-1}, g1 = gamma_k; amp is the
-// amplitude of the sin term and A the underdamped velocity coefficient.
+// Bias arguments of the steps of a block: step s of the block (s = 0 .. kBlockSteps - 1) takes
+// g0 = fmaf(slope, s, base) and g1 = fmaf(slope, s + 1, base).  For the overdamped Euler step the
+// line is pre-multiplied by dt (g1 = dt gamma_k), so that bias and noise form one addend that
+// does not depend on the phase (off the step's serial chain); the other kinds take gamma itself.
+template <int M, int H>
+__device__ __forceinline__ void bias_line(float gs, float nudt, float dt, float &base, float &slope) {
+    if constexpr (M == kOver && H == kEuler) {
+        base = __fmul_rn(dt, gs);
+        slope = __fmul_rn(dt, nudt);
+    } else {
+        base = gs;
+        slope = nudt;
+    }
+}
+
+// One step with noise increment sigma z = rr * trig; g0, g1 = the bias at the two ends of the
+// step (gamma_{k-1}, gamma_k; for the overdamped Euler step dt gamma_{k-1}, dt gamma_k, see
+// bias_line); amp is the amplitude of the sin term and A the underdamped velocity coefficient.
 // Euler-Maruyama (H = 0; Alg. 1 / Alg. 3, both updates read the state of the previous step):
 //   underdamped: phi += v dt;  v = A v + (g1 - amp sin phi_old) dt + sigma z     [A = 1 - alpha dt]
-//   overdamped : phi += (g1 - amp sin phi_old) dt + sigma z
+//   overdamped : phi = (phi + (dt gamma_k + sigma z)) - (amp dt) sin phi_old
 // Stochastic Heun (H = 1; predictor with the step's normal, corrector averaging the drift over
 // both ends of the step):
 //   overdamped : f0 = g0 - amp sin phi;  p = phi + f0 dt + sigma z;  f1 = g1 - amp sin p
@@ -144,13 +160,14 @@ __device__ __forceinline__ void step_f32(float &r, float &v, float rr, float tri
                                          float g1, float dt, float A, float amp) {
     if constexpr (H == kEuler) {
         const float s = __sinf(r);
-        const float f = fmaf(-amp, s, g1);
         if constexpr (M == kUnder) {
+            const float f = fmaf(-amp, s, g1);
             const float vn = fmaf(A, v, fmaf(dt, f, __fmul_rn(rr, trig)));
             r = fmaf(dt, v, r);
             v = vn;
         } else {
-            r = fmaf(rr, trig, fmaf(dt, f, r));
+            const float q = fmaf(rr, trig, g1);   // g1 = dt gamma_k: independent of the phase
+            r = fmaf(__fmul_rn(-amp, dt), s, __fadd_rn(r, q));
         }
     } else {
         const float n = __fmul_rn(rr, trig);
