@@ -9,10 +9,23 @@ a "step" of this benchmark is one engine iteration (one resident-kernel launch o
 Euler-Maruyama steps per lane, the completion scan and the status read-back), and the metric
 is the steady-state throughput of useful trajectory-steps (escapes/s beside it).
 
+Launch shape: trajectories per thread and threads per block come from the autotuner, measured on
+a short run of the same sweep (--no-autotune keeps --traj-per-thread / --block).
+
 Timing: W untimed iterations, then K iterations each bracketed by CUDA events on the engine's
 stream; between timed iterations L2 is flushed by writing a 512 MiB buffer (outside the events).
-Under torchrun every rank runs its own engine on its own trajectory ids (weak scaling); the
-reported value sums all ranks' steps and divides by the slowest rank's time.
+SM clocks and throttle reasons are sampled by nvidia-smi every 50 ms; only samples inside the
+timed region are summarised.  Under torchrun every rank runs its own engine on its own trajectory
+ids (weak scaling); the reported value sums all ranks' steps and divides by the slowest rank's
+time.
+
+Further fields of the one JSON line: `roofline` (XU-pipe bound of the resident kernel, ncu
+traffic per launch), `e2e` (a fresh engine driven through the C ABI from host memory),
+`fp64_plain` (the one-trajectory-per-thread FP64 kernel on the same GPU, its FP32 twin and a
+library FP64 GEMM rate for context), `fp32_engine_point` (accuracy of the engine on one point),
+`heun` (the same sweep with the stochastic Heun integrator), `other_workloads` (the ramp sweep
+and the 256-set uneven batch), `autotune`, `serving` (Poisson request stream: p50 / p99
+latency), `cpu_baseline` (the FP64 oracle on the host cores, a bounded sample), `clocks`.
 
 --impl reference times the FP64 CPU oracle (the method's plain restatement) on the host cores
 on a bounded sample of the same workload.
