@@ -339,7 +339,7 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
                 bm_pair_f32(x.x, x.y, L[t].bmc, rr[t][2 * h], tg[t][4 * h], tg[t][4 * h + 1]);
                 bm_pair_f32(x.z, x.w, L[t].bmc, rr[t][2 * h + 1], tg[t][4 * h + 2], tg[t][4 * h + 3]);
             }
-            bias_line<M, H>(fmaf(L[t].nudt, L[t].Jf, L[t].gb), L[t].nudt, L[t].dt, gs[t], gsl[t]);
+            bias_line(fmaf(L[t].nudt, L[t].Jf, L[t].gb), L[t].nudt, L[t].dt, gs[t], gsl[t]);
         }
         // The block's steps without a branch: each lane only tracks the largest phase of the block.
         // In the rare block where it reached the lane's bound hb, the lane's block is replayed
@@ -358,8 +358,8 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
             for (int t = 0; t < T; ++t) {
                 step_f32<M, H>(L[t].r, L[t].v, rr[t][s >> 1], tg[t][s],
                                fmaf(gsl[t], static_cast<float>(s), gs[t]),
-                               fmaf(gsl[t], static_cast<float>(s + 1), gs[t]), L[t].dt, L[t].A,
-                               L[t].amp);
+                               fmaf(gsl[t], static_cast<float>(s) + kBiasEnd<H>, gs[t]),
+                               L[t].dt, L[t].A, L[t].amp);
                 mx[t] = fmaxf(mx[t], L[t].r);
             }
         }
@@ -385,8 +385,8 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
                     for (int s = 0; s < kBlockSteps; ++s) {
                         step_f32<M, H>(L[t].r, L[t].v, rr[t][s >> 1], tg[t][s],
                                        fmaf(gsl[t], static_cast<float>(s), gs[t]),
-                                       fmaf(gsl[t], static_cast<float>(s + 1), gs[t]), L[t].dt,
-                                       L[t].A, L[t].amp);
+                                       fmaf(gsl[t], static_cast<float>(s) + kBiasEnd<H>, gs[t]),
+                                       L[t].dt, L[t].A, L[t].amp);
                         if (L[t].r >= L[t].hb) phase_event(L[t], E, s);
                     }
                 }

@@ -124,66 +124,71 @@ struct StepConstF32 {
 enum : int { kUnder = 0, kOver = 1 };
 enum : int { kEuler = 0, kHeun = 1 };
 
-// Bias arguments of the steps of a block: step s of the block (s = 0 .. kBlockSteps - 1) takes
-// g0 = fmaf(slope, s, base) and g1 = fmaf(slope, s + 1, base).  For the overdamped Euler step the
-// line is pre-multiplied by dt (g1 = dt gamma_k), so that bias and noise form one addend that
-// does not depend on the phase (off the step's serial chain); the other kinds take gamma itself.
-template <int M, int H>
+// Bias arguments of the steps of a block.  Every FP32 step takes its bias already multiplied by
+// dt, so bias and noise form addends that do not depend on the state (off the step's serial
+// chain): the block's line is base = dt gs, slope = dt nu dt, and step s of the block
+// (s = 0 .. kBlockSteps - 1) takes b0 = fmaf(slope, s, base) = dt gamma_{k-1} and
+// b1 = fmaf(slope, s + kBiasEnd<H>, base): dt gamma_k for Euler, the midpoint
+// dt (gamma_{k-1} + gamma_k) / 2 for Heun (s + 1/2 is exact).
+template <int H>
+constexpr float kBiasEnd = H == kHeun ? 0.5f : 1.0f;
+
 __device__ __forceinline__ void bias_line(float gs, float nudt, float dt, float &base, float &slope) {
-    if constexpr (M == kOver && H == kEuler) {
-        base = __fmul_rn(dt, gs);
-        slope = __fmul_rn(dt, nudt);
-    } else {
-        base = gs;
-        slope = nudt;
-    }
+    base = __fmul_rn(dt, gs);
+    slope = __fmul_rn(dt, nudt);
 }
 
-// One step with noise increment sigma z = rr * trig; g0, g1 = the bias at the two ends of the
-// step (gamma_{k-1}, gamma_k; for the overdamped Euler step dt gamma_{k-1}, dt gamma_k, see
-// bias_line); amp is the amplitude of the sin term and A the underdamped velocity coefficient.
-// Euler-Maruyama (H = 0; Alg. 1 / Alg. 3, both updates read the state of the previous step):
-//   underdamped: phi += v dt;  v = A v + (g1 - amp sin phi_old) dt + sigma z     [A = 1 - alpha dt]
-//   overdamped : phi = (phi + (dt gamma_k + sigma z)) - (amp dt) sin phi_old
+// One step with noise increment sigma z = rr * trig and dt-scaled bias b0, b1 (see bias_line);
+// amp is the amplitude of the sin term, c = -amp dt, A the underdamped velocity coefficient.
+// Euler-Maruyama (H = 0; Alg. 1 / Alg. 3, both updates read the state of the previous step;
+// b1 = dt gamma_k):
+//   underdamped: v' = (A v + (b1 + sigma z)) + c sin phi;  phi' = phi + v dt      [A = 1 - alpha dt]
+//   overdamped : phi' = (phi + (b1 + sigma z)) + c sin phi
 // Stochastic Heun (H = 1; predictor with the step's normal, corrector averaging the drift over
-// both ends of the step):
-//   overdamped : f0 = g0 - amp sin phi;  p = phi + f0 dt + sigma z;  f1 = g1 - amp sin p
-//                phi += (f0 + f1) dt / 2 + sigma z
-//   underdamped: a0 = A v - amp sin phi + g0;  p = phi + v dt;  q = v + a0 dt + sigma z
-//                a1 = A q - amp sin p + g1;  phi += (v + q) dt / 2;  v += (a0 + a1) dt / 2 + sigma z
-//                                                                               [A = -alpha]
+// both ends of the step; b0 = dt gamma_{k-1}, b1 = dt (gamma_{k-1} + gamma_k) / 2):
+//   overdamped : p = (phi + (b0 + sigma z)) + c sin phi
+//                phi' = (phi + (b1 + sigma z)) + (c / 2) (sin phi + sin p)
+//   underdamped: q = ((v + (b0 + sigma z)) + (A dt) v) + c sin phi;  p = phi + v dt
+//                v' = ((v + (b1 + sigma z)) + (A dt / 2)(v + q)) + (c / 2)(sin phi + sin p)
+//                phi' = phi + (dt / 2)(v + q)                                       [A = -alpha]
+//   i.e. a0 = A v - amp sin phi + gamma_{k-1}, q = v + a0 dt + sigma z,
+//   a1 = A q - amp sin p + gamma_k, v' = v + (a0 + a1) dt / 2 + sigma z.
 // r is the phase wrapped to [-pi, pi); the caller restores the range and counts windings.
 // Every rounding is explicit (fmaf / __fmul_rn / __fadd_rn), so all kernels that take this step
 // agree bit for bit.
 template <int M, int H>
-__device__ __forceinline__ void step_f32(float &r, float &v, float rr, float trig, float g0,
-                                         float g1, float dt, float A, float amp) {
+__device__ __forceinline__ void step_f32(float &r, float &v, float rr, float trig, float b0,
+                                         float b1, float dt, float A, float amp) {
+    const float c = __fmul_rn(-amp, dt);
     if constexpr (H == kEuler) {
         const float s = __sinf(r);
+        const float q = fmaf(rr, trig, b1);    // dt gamma_k + sigma z: independent of the state
         if constexpr (M == kUnder) {
-            const float f = fmaf(-amp, s, g1);
-            const float vn = fmaf(A, v, fmaf(dt, f, __fmul_rn(rr, trig)));
+            const float vn = fmaf(c, s, fmaf(A, v, q));
             r = fmaf(dt, v, r);
             v = vn;
         } else {
-            const float q = fmaf(rr, trig, g1);   // g1 = dt gamma_k: independent of the phase
-            r = fmaf(__fmul_rn(-amp, dt), s, __fadd_rn(r, q));
+            r = fmaf(c, s, __fadd_rn(r, q));
         }
     } else {
-        const float n = __fmul_rn(rr, trig);
-        const float hdt = __fmul_rn(0.5f, dt);
+        const float hc = __fmul_rn(0.5f, c);
+        const float q0 = fmaf(rr, trig, b0);
+        const float qm = fmaf(rr, trig, b1);
+        const float s0 = __sinf(r);
         if constexpr (M == kUnder) {
-            const float a0 = fmaf(A, v, fmaf(-amp, __sinf(r), g0));
+            const float dA = __fmul_rn(dt, A);
+            const float hdA = __fmul_rn(0.5f, dA);
+            const float hdt = __fmul_rn(0.5f, dt);
+            const float q = fmaf(c, s0, fmaf(dA, v, __fadd_rn(v, q0)));
             const float p = fmaf(dt, v, r);
-            const float q = __fadd_rn(fmaf(dt, a0, v), n);
-            const float a1 = fmaf(A, q, fmaf(-amp, __sinf(p), g1));
-            r = fmaf(hdt, __fadd_rn(v, q), r);
-            v = __fadd_rn(fmaf(hdt, __fadd_rn(a0, a1), v), n);
+            const float vq = __fadd_rn(v, q);
+            const float s1 = __sinf(p);
+            v = fmaf(hc, __fadd_rn(s0, s1), fmaf(hdA, vq, __fadd_rn(v, qm)));
+            r = fmaf(hdt, vq, r);
         } else {
-            const float f0 = fmaf(-amp, __sinf(r), g0);
-            const float p = __fadd_rn(fmaf(dt, f0, r), n);
-            const float f1 = fmaf(-amp, __sinf(p), g1);
-            r = __fadd_rn(fmaf(hdt, __fadd_rn(f0, f1), r), n);
+            const float p = fmaf(c, s0, __fadd_rn(r, q0));
+            const float s1 = __sinf(p);
+            r = fmaf(hc, __fadd_rn(s0, s1), __fadd_rn(r, qm));
         }
     }
 }

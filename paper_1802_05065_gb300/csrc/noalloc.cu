@@ -128,11 +128,11 @@ __global__ void __launch_bounds__(kBlock) noalloc_kernel(NoAllocArgs a) {
             bm_pair_f32(x.z, x.w, a.bmc, rr[2 * h + 1], tg[4 * h + 2], tg[4 * h + 3]);
         }
         float gs, gsl;
-        bias_line<M, H>(fmaf(a.nudt, L.Jf, L.gb), a.nudt, a.dt, gs, gsl);
+        bias_line(fmaf(a.nudt, L.Jf, L.gb), a.nudt, a.dt, gs, gsl);
 #pragma unroll
         for (int s = 0; s < kBlockSteps; ++s) {
             step_f32<M, H>(L.r, L.v, rr[s >> 1], tg[s], fmaf(gsl, static_cast<float>(s), gs),
-                           fmaf(gsl, static_cast<float>(s + 1), gs), a.dt, a.A, a.amp);
+                           fmaf(gsl, static_cast<float>(s) + kBiasEnd<H>, gs), a.dt, a.A, a.amp);
             if (L.r >= L.hb) {
                 const float eb = fmaf(-kTwoPiF, static_cast<float>(L.w - a.w0), a.eb0);
                 if (L.r >= eb) {

@@ -115,11 +115,12 @@ __global__ void __launch_bounds__(256) plain_f32_kernel(PlainArgs a) {
                 bm_pair_f32(x.z, x.w, a.bmc_f, rr[2 * h + 1], tg[4 * h + 2], tg[4 * h + 3]);
             }
             float gs, gsl;
-            bias_line<M, H>(fmaf(a.nudt_f, Jf, gb), a.nudt_f, a.dt_f, gs, gsl);
+            bias_line(fmaf(a.nudt_f, Jf, gb), a.nudt_f, a.dt_f, gs, gsl);
 #pragma unroll
             for (int s = 0; s < kBlockSteps; ++s) {
                 step_f32<M, H>(r, v, rr[s >> 1], tg[s], fmaf(gsl, static_cast<float>(s), gs),
-                               fmaf(gsl, static_cast<float>(s + 1), gs), a.dt_f, a.A_f, a.amp_f);
+                               fmaf(gsl, static_cast<float>(s) + kBiasEnd<H>, gs), a.dt_f, a.A_f,
+                               a.amp_f);
                 if (r >= hb) {
                     // threshold in the current cell: eb = phi* - 2 pi w (same rounding as the engine)
                     const float eb = fmaf(-kTwoPiF, static_cast<float>(w - a.w0), a.eb0_f);
