@@ -62,5 +62,7 @@ def test_plain_kernel_efficiency_follows_appendix_a():
     e_bal, te_bal, _ = _timed_engine(m, balanced, n, 3)
     eff_engine = (e_noisy / te_noisy) / (e_bal / te_bal)
     pred = lb.greedy_efficiency(s_noisy, lanes) / lb.greedy_efficiency(s_bal, lanes)
+    print(f"efficiency: plain {eff_plain:.3f} (App. A CTA {eff_cta:.3f}, warp {eff_warp:.3f}), "
+          f"engine {eff_engine:.3f} (list scheduling {pred:.3f})")
     assert 0.95 * pred <= eff_engine <= 1.02, (eff_engine, pred)
     assert eff_engine > 1.5 * eff_plain, (eff_engine, eff_plain)
