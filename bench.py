@@ -500,6 +500,25 @@ def run_ours(args):
         mix["ramp_sweep"]["workload"] = "ramp sweep nu {1e-5..1e-8}, 4 x 2^20 trajectories"
         mix["uneven_batch"]["workload"] = ("uneven batch, 256 sets, 2^12..2^18 trajectories, "
                                            "half ramped, one engine")
+        # time to solution against the number of realisations (the analogue of the paper's
+        # execution time vs N_r, Sec. III.C): one request of the gamma = 0.9, D = 0.2 point run
+        # to completion; below the lane count the longest trajectories set the time (App. A)
+        tts = []
+        with pkg.Engine(local, chunk_steps=16384, traj_per_thread=args.traj_per_thread,
+                        threads_per_block=args.block) as e5:
+            lanes5 = e5.counters()["lanes"]
+            for lg in (12, 14, 16, 18, 20, 22):
+                b0 = e5.counters()
+                t5 = time.perf_counter()
+                r5 = e5.wait(e5.submit(pkg.params_from(pts[11]), 2**lg, 7), 600.0)
+                w5 = time.perf_counter() - t5
+                b1 = e5.counters()
+                tts.append({"n_traj": 2**lg, "seconds": w5,
+                            "kernel_ms": b1["kernel_ms"] - b0["kernel_ms"],
+                            "steps_per_s": (b1["useful_steps"] - b0["useful_steps"]) / w5,
+                            "mean_fpt": r5.mean})
+        mix["time_to_solution"] = {"point": "gamma=0.9 D=0.2, one request run to completion",
+                                   "lanes": lanes5, "runs": tts}
 
     serving = None
     if not args.no_serving and rank == 0 and world == 1:
