@@ -223,7 +223,10 @@ class Engine:
         c.device = device
         c.stream = stream or None
         c.use_graph = int(cfg.pop("use_graph", 1))
+        known = {f[0] for f in EngineConfig._fields_}
         for k, v in cfg.items():
+            if k not in known or k in ("device", "stream"):
+                raise TypeError(f"unknown engine option {k!r}")
             setattr(c, k, v)
         h = ctypes.c_void_p()
         _check(L.fpt_create(ctypes.byref(c), ctypes.byref(h)))

@@ -117,3 +117,8 @@ def test_product_path_has_no_oracle_dependency():
                 src = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in src and "from oracle" not in src, f
                 assert "fpt_oracle" not in src and "oracle_" not in src, f
+
+
+def test_engine_rejects_unknown_options(lib):
+    with pytest.raises(TypeError):
+        lib.Engine(0, chunk_step=4096)      # misspelt option is an error, not ignored
