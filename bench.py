@@ -62,7 +62,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--chunk-steps", type=int, default=65536)
     ap.add_argument("--traj-per-thread", type=int, default=1)
-    ap.add_argument("--block", type=int, default=512)
+    ap.add_argument("--block", type=int, default=640)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -243,7 +243,7 @@ def run_reference(args):
 # (ncu capture summarised in profiles/engine_chunk_kernel__overdamped_sweep.md): the lane state is
 # read and written once per launch, whatever the number of steps, so a 65 536-step launch moves
 # the same bytes as the captured 4096-step one.
-TRAFFIC_BYTES_PER_LAUNCH = 2.92e6
+TRAFFIC_BYTES_PER_LAUNCH = 3.63e6
 
 
 def roofline_model(n_sm: int, f_mhz: float):

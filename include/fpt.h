@@ -140,7 +140,7 @@ typedef struct {
     int32_t max_requests;       /* resident request slots (1 .. 1024; 0 = 256) */
     uint64_t mem_budget_bytes;  /* device memory the engine may allocate (0 = 25 % of free) */
     void *stream;               /* cudaStream_t to run on (NULL = engine-owned stream) */
-    int32_t threads_per_block;  /* 0 = default: 512 with one trajectory per thread, 256 with two */
+    int32_t threads_per_block;  /* 0 = default: 640 with one trajectory per thread, 256 with two */
     int32_t blocks_per_sm;      /* 0 = as many as fit */
     int32_t traj_per_thread;    /* 1 or 2 (0 = default 1) */
     uint32_t chunk_steps;       /* steps per resident-kernel launch, multiple of 16 (0 = 16384) */

@@ -41,7 +41,7 @@ def _measure(requests, device, cfg, iters, chunk):
 def tune(requests, device: int = 0, iters: int = 3, chunk: int = 8192,
          grid=None, overhead: float = 0.02, save: bool = True) -> dict:
     """requests: list of (params dict, n_traj, seed).  Returns the best configuration."""
-    grid = grid or {"traj_per_thread": (1, 2), "threads_per_block": (128, 256, 512),
+    grid = grid or {"traj_per_thread": (1, 2), "threads_per_block": (128, 256, 512, 640),
                     "blocks_per_sm": (0,)}
     keys = sorted(grid)
     trials = []

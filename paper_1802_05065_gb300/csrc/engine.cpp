@@ -538,10 +538,10 @@ fpt_status create_impl(const fpt_engine_config *cfg_in, fpt_engine *e) {
     if (e->maxr > 1024) return fail(e, FPT_EINVAL, "max_requests must be <= 1024");
     e->T = cfg.traj_per_thread > 0 ? cfg.traj_per_thread : 1;
     if (e->T != 1 && e->T != 2) return fail(e, FPT_EINVAL, "traj_per_thread must be 1 or 2");
-    const int max_block = e->T == 1 ? 512 : 256;
+    const int max_block = e->T == 1 ? 640 : 256;
     e->block = cfg.threads_per_block > 0 ? cfg.threads_per_block : max_block;
     if (e->block % 32 || e->block > max_block)
-        return fail(e, FPT_EINVAL, "threads_per_block: multiple of 32, <= 512 (one trajectory per "
+        return fail(e, FPT_EINVAL, "threads_per_block: multiple of 32, <= 640 (one trajectory per "
                                    "thread) or <= 256 (two)");
     const uint32_t chunk = cfg.chunk_steps ? cfg.chunk_steps : 16384;
     if (chunk % kBlockSteps || chunk > (1u << 24))
