@@ -495,8 +495,12 @@ def run_ours(args):
     if not args.no_mix and rank == 0:
         ramp = [(d, n_traj, d["seed"]) for d in workloads.ramp_sweep(n_traj=n_traj)]
         ub = [(d, d["n_traj"], d["seed"]) for d in workloads.uneven_batch()]
+        li = workloads.li07_switching()
         mix = {"ramp_sweep": _leg(ramp, 5, 65536),
-               "uneven_batch": _leg(ub, 10, 16384)}
+               "uneven_batch": _leg(ub, 10, 16384),
+               "li07_device": _leg([(li, li["n_traj"], li["seed"])], 5, 65536)}
+        mix["li07_device"]["workload"] = ("the Fig. 10b junction (Li07 parameters), 30 000 "
+                                          "trajectories at the paper's ramp, first iterations")
         mix["ramp_sweep"]["workload"] = "ramp sweep nu {1e-5..1e-8}, 4 x 2^20 trajectories"
         mix["uneven_batch"]["workload"] = ("uneven batch, 256 sets, 2^12..2^18 trajectories, "
                                            "half ramped, one engine")
