@@ -112,7 +112,7 @@ struct fpt_engine {
     SlotDev *h_slots = nullptr;
     SlotCtl *h_ctl = nullptr, *h_ctl_init = nullptr;
     int *h_caps = nullptr, *h_act = nullptr, *h_act_count = nullptr;
-    int *h_preempt = nullptr, *h_flags = nullptr;   // flags: vacate[kNumKinds], strict
+    int *h_preempt = nullptr, *h_flags = nullptr;   // flags: vacate[kNumKinds], strict, claim_warps
     uint64_t preempted = 0;
     unsigned long long *h_counters = nullptr;
     int *h_state = nullptr;
@@ -313,6 +313,28 @@ void build_lists(fpt_engine *e) {
     for (int k = 0; k <= kNumKinds; ++k) e->h_flags[k] = 0;
     for (int s = 0; s < e->maxr; ++s)
         if (e->h_preempt[s]) e->h_flags[kNumKinds] = 1;   // keep a suspending request's lanes from refilling
+    // With fewer trajectories in flight and queued than lanes, only the first warps of every CTA
+    // claim new work, so the busy warps spread over all SMs instead of filling a few of them.
+    {
+        int64_t work = 0;
+        for (int s = 0; s < e->maxr; ++s) {
+            if (!e->slot_req[s]) continue;
+            const Request &R = *e->reqs[e->slot_req[s]];
+            if (R.phase != kRunning || R.suspending) continue;
+            const SlotCtl &C = e->h_ctl[s];
+            if (C.state == kSlotActive) {
+                const uint64_t head = std::min<uint64_t>(C.head, R.n_traj);
+                work += static_cast<int64_t>(R.n_traj - head) + std::max(C.inflight, 0) +
+                        std::max(C.park_avail, 0);
+            } else {
+                work += static_cast<int64_t>(R.n_traj);   // admitted for the coming launch
+            }
+        }
+        const int64_t per_warp = 32ll * e->T * e->grid;
+        const int64_t warps = (work + per_warp - 1) / per_warp;
+        e->h_flags[kNumKinds + 1] =
+            static_cast<int>(std::min<int64_t>(std::max<int64_t>(warps, 1), e->block / 32));
+    }
     if (active < 2) return;
     int64_t deficit[kNumKinds] = {0, 0, 0, 0};
     bool over[kNumKinds] = {false, false, false, false};
@@ -357,7 +379,7 @@ fpt_status enqueue_iteration(fpt_engine *e) {
     }
     CK(cudaMemcpyAsync(e->d_caps, e->h_caps, e->maxr * sizeof(int), cudaMemcpyHostToDevice, e->stream));
     CK(cudaMemcpyAsync(e->d_preempt, e->h_preempt, e->maxr * sizeof(int), cudaMemcpyHostToDevice, e->stream));
-    CK(cudaMemcpyAsync(e->d_vacate, e->h_flags, (kNumKinds + 1) * sizeof(int), cudaMemcpyHostToDevice,
+    CK(cudaMemcpyAsync(e->d_vacate, e->h_flags, (kNumKinds + 2) * sizeof(int), cudaMemcpyHostToDevice,
                        e->stream));
     CK(cudaMemcpyAsync(e->d_act, e->h_act, kNumKinds * e->maxr * sizeof(int), cudaMemcpyHostToDevice,
                        e->stream));
@@ -573,9 +595,9 @@ fpt_status create_impl(const fpt_engine_config *cfg_in, fpt_engine *e) {
     CK(cudaMalloc(&e->d_act, kNumKinds * R * sizeof(int)));
     CK(cudaMalloc(&e->d_act_count, kNumKinds * sizeof(int)));
     CK(cudaMalloc(&e->d_preempt, R * sizeof(int)));
-    CK(cudaMalloc(&e->d_vacate, (kNumKinds + 1) * sizeof(int)));   // vacate[kNumKinds], strict
+    CK(cudaMalloc(&e->d_vacate, (kNumKinds + 2) * sizeof(int)));   // vacate[kNumKinds], strict, claim
     CK(cudaMemsetAsync(e->d_preempt, 0, R * sizeof(int), e->stream));
-    CK(cudaMemsetAsync(e->d_vacate, 0, (kNumKinds + 1) * sizeof(int), e->stream));
+    CK(cudaMemsetAsync(e->d_vacate, 0, (kNumKinds + 2) * sizeof(int), e->stream));
     const size_t L = e->lanes;
     CK(cudaMalloc(&e->d_lane_mem, L * 4 * 10));
     const unsigned nwarps = static_cast<unsigned>(e->grid) * e->block / 32;
@@ -612,9 +634,9 @@ fpt_status create_impl(const fpt_engine_config *cfg_in, fpt_engine *e) {
     CK(cudaMallocHost(&e->h_act, kNumKinds * R * sizeof(int)));
     CK(cudaMallocHost(&e->h_act_count, kNumKinds * sizeof(int)));
     CK(cudaMallocHost(&e->h_preempt, R * sizeof(int)));
-    CK(cudaMallocHost(&e->h_flags, (kNumKinds + 1) * sizeof(int)));
+    CK(cudaMallocHost(&e->h_flags, (kNumKinds + 2) * sizeof(int)));
     std::memset(e->h_preempt, 0, R * sizeof(int));
-    std::memset(e->h_flags, 0, (kNumKinds + 1) * sizeof(int));
+    std::memset(e->h_flags, 0, (kNumKinds + 2) * sizeof(int));
     CK(cudaMallocHost(&e->h_counters, kCntCount * sizeof(unsigned long long)));
     std::memset(e->h_ctl, 0, R * sizeof(SlotCtl));
     std::memset(e->h_caps, 0, R * sizeof(int));
@@ -630,6 +652,7 @@ fpt_status create_impl(const fpt_engine_config *cfg_in, fpt_engine *e) {
     d.preempt = e->d_preempt;
     d.vacate = e->d_vacate;
     d.strict = e->d_vacate + kNumKinds;
+    d.claim_warps = e->d_vacate + kNumKinds + 1;
     d.act_count = e->d_act_count;
     d.warp_kind = e->d_warp_kind;
     d.warp_cursor = e->d_warp_cursor;

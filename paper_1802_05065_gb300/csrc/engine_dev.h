@@ -92,6 +92,8 @@ struct EngineDev {
     int *preempt;           // [max_requests] lanes to suspend at the end of this launch
     int *vacate;            // [kNumKinds] whole warps of each kind to suspend at the end of this launch
     const int *strict;      // [1] 1: never exceed the caps (someone is starved)
+    const int *claim_warps; // [1] warps of each CTA (counted from warp 0) that claim new work:
+                            // when there is less work than lanes it is spread over every SM
     const int *act_list;    // [kNumKinds][max_requests] claimable slots per kind
     const int *act_count;   // [kNumKinds]
     LaneSoA lanes;

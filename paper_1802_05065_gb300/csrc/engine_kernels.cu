@@ -243,6 +243,7 @@ __device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, int kin
         total += __popc(idle[t]);
     }
     if (total == 0) return;
+    if (static_cast<int>(threadIdx.x >> 5) >= *E.claim_warps) return;   // spread scarce work
     const int cnt = E.act_count[kind];
     if (cnt <= 0) return;
     const int *list = E.act_list + kind * E.max_requests;
