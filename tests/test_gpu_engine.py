@@ -359,3 +359,24 @@ def test_restore_rejects_foreign_or_truncated_blobs(lib):
             assert ei.value.status == -1
         res = eng.wait(eng.restore(blob), 600.0)
         assert res.n_used == 4000
+
+
+@pytest.mark.parametrize("integrator", ["em", "heun"])
+def test_noise_free_running_state_period(lib, api, integrator):
+    """D = 0, gamma = 1.5 > 1 (no well): every trajectory runs down the washboard and crosses
+    phi0 + 2 pi after the running period 2 pi / sqrt(gamma^2 - 1) = 5.6199, i.e. at step
+    ceil(T / dt) = 5620 of a per-step test (the FP64 oracle gives exactly that for both
+    integrators); the FP32 engine lands within 3 steps, identically for every trajectory and for
+    the plain kernel."""
+    d = workloads.base(model="overdamped", D=0.0, gamma0=1.5, dt=1e-3, phi0=0.0,
+                       threshold=2 * math.pi, threshold_mode="from_start", max_steps=10**6,
+                       integrator=integrator)
+    n = 3000
+    with _engine(lib, chunk_steps=2048) as eng:
+        rid = eng.submit(lib_params(d, keep_per_traj=1), n, 1)
+        eng.wait(rid, 600.0)
+        k = eng.per_traj_steps(rid, n)
+    assert (k == k[0]).all()
+    assert (k == api.run_plain(d, n, 1).cpu().numpy()).all()
+    want = math.ceil(mfpt.running_period(1.5) / 1e-3)
+    assert abs(int(k[0]) - want) <= 3, (k[0], want)
