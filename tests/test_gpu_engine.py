@@ -380,3 +380,29 @@ def test_noise_free_running_state_period(lib, api, integrator):
     assert (k == api.run_plain(d, n, 1).cpu().numpy()).all()
     want = math.ceil(mfpt.running_period(1.5) / 1e-3)
     assert abs(int(k[0]) - want) <= 3, (k[0], want)
+
+
+@pytest.mark.parametrize("output", ["time", "bias"])
+def test_per_trajectory_observables_and_censoring(lib, output):
+    """fpt_per_traj: x = k dt (time) or gamma0 + (nu dt) k (bias, Alg. 3) in IEEE double for
+    every escaped trajectory, equal to the oracle's definition; censored trajectories (a budget
+    that only part of them meets) are -1 (time) or NaN (bias), and counted in n_censored."""
+    if output == "bias":
+        d = workloads.scaled(RAMP, max_steps=98000)          # bias 0.98: about half switch
+    else:
+        d = workloads.scaled(CONST_UNDER, max_steps=200000)
+    n = 4000
+    with _engine(lib, chunk_steps=4096) as eng:
+        rid = eng.submit(lib_params(d, keep_per_traj=1), n, 23)
+        res = eng.wait(rid, 600.0)
+        k = eng.per_traj_steps(rid, n)
+        x = eng.per_traj(rid, n)
+    p = oracle.params_from(d)
+    cens = k < 0
+    assert 0 < cens.sum() < n and res.n_censored == cens.sum()
+    want = np.array([stats.observable(p, int(v)) for v in k[~cens]])
+    assert (x[~cens] == want).all()
+    if output == "bias":
+        assert np.isnan(x[cens]).all()
+    else:
+        assert (x[cens] == -1.0).all()
