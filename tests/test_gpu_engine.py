@@ -406,3 +406,24 @@ def test_per_trajectory_observables_and_censoring(lib, output):
         assert np.isnan(x[cens]).all()
     else:
         assert (x[cens] == -1.0).all()
+
+
+@pytest.mark.parametrize("max_steps", [1, 3, 5, 17, 33])
+def test_tiny_step_budgets(lib, api, max_steps):
+    """Budgets shorter than, equal to and just past one 16-step block: the engine runs whole
+    blocks, so it integrates past the budget and must count only escapes at k <= max_steps.
+    Per trajectory it equals the plain kernel; the escape count per step matches the FP64
+    oracle's within binomial noise, and nothing beyond the budget is counted."""
+    d = workloads.base(model="overdamped", D=0.5, gamma0=0.5, dt=0.01, threshold=0.3,
+                       threshold_mode="from_start", max_steps=max_steps)
+    n = 20000
+    with _engine(lib, chunk_steps=1024) as eng:
+        rid, res = _run(eng, d, n, 9, keep_per_traj=1)
+        k = eng.per_traj_steps(rid, n)
+    assert (k == api.run_plain(d, n, 9).cpu().numpy()).all()
+    assert k.max() <= max_steps and res.n_escaped == (k >= 0).sum()
+    assert res.steps_total == int(k[k >= 0].sum()) + max_steps * int((k < 0).sum())
+    r = oracle.run(oracle.params_from(d), 9, 4000)
+    f_gpu, f_ref = (k >= 0).mean(), (r >= 0).mean()
+    se = math.sqrt(max(f_ref * (1 - f_ref), 1e-4) / 4000 + max(f_gpu * (1 - f_gpu), 1e-4) / n)
+    assert abs(f_gpu - f_ref) < 4 * se, (f_gpu, f_ref)
