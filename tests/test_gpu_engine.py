@@ -427,3 +427,23 @@ def test_tiny_step_budgets(lib, api, max_steps):
     f_gpu, f_ref = (k >= 0).mean(), (r >= 0).mean()
     se = math.sqrt(max(f_ref * (1 - f_ref), 1e-4) / 4000 + max(f_gpu * (1 - f_gpu), 1e-4) / n)
     assert abs(f_gpu - f_ref) < 4 * se, (f_gpu, f_ref)
+
+
+@pytest.mark.parametrize("integrator", ["em", "heun"])
+def test_hundred_windings_to_the_threshold(lib, api, integrator):
+    """D = 0, gamma = 1.5, threshold 100 periods (200 pi) from the start: the wrapped phase must
+    count 99 upper wraps and then find the threshold in its cell.  The FP64 oracle (unwrapped
+    phase) crosses at step 561 986 for both integrators.  The FP32 phase adds increments of
+    ~1.5e-3 to values of order pi, so each step rounds at ~1e-4 of its increment; measured over
+    these 5.6e5 steps that accumulates to 14 steps (2.5e-5 of the time), asserted below 1e-4."""
+    d = workloads.base(model="overdamped", D=0.0, gamma0=1.5, dt=1e-3, phi0=0.0,
+                       threshold=200 * math.pi, threshold_mode="from_start", max_steps=10**7,
+                       integrator=integrator)
+    p = oracle.params_from(d)
+    esc, k_ref, *_ = oracle.trajectory(p, 0, 0)
+    assert esc
+    with _engine(lib, chunk_steps=16384) as eng:
+        rid, res = _run(eng, d, 64, 1, keep_per_traj=1)
+        k = eng.per_traj_steps(rid, 64)
+    assert (k == k[0]).all() and (k == api.run_plain(d, 64, 1).cpu().numpy()).all()
+    assert abs(int(k[0]) - k_ref) <= 1e-4 * k_ref, (k[0], k_ref)
