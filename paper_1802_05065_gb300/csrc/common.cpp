@@ -50,7 +50,6 @@ bool decode(const fpt_params *p, Decoded *d, std::string *err) {
 
     d->model = p->model;
     d->integrator = p->integrator;
-    d->kind = p->model + 2 * p->integrator;
     d->output = p->output;
     d->alpha = p->model == FPT_UNDERDAMPED ? p->alpha : 0.0;
     d->D = p->D;
@@ -79,6 +78,8 @@ bool decode(const fpt_params *p, Decoded *d, std::string *err) {
     d->amp_f = static_cast<float>(d->amp);
     d->bmc_f = static_cast<float>(-2.0 * M_LN2 * d->sigma * d->sigma);
     d->nudt_f = static_cast<float>(d->nudt);
+    // code path: model, integrator, and whether the single-precision bias ramps at all
+    d->kind = p->model + 2 * p->integrator + 4 * (d->nudt_f != 0.0f ? 1 : 0);
     d->v0_f = static_cast<float>(d->v0);
     const double two_pi = 2.0 * M_PI;
     double w0 = std::floor((d->phi0 + M_PI) / two_pi);

@@ -292,7 +292,7 @@ fpt_status admit(fpt_engine *e) {
 // the end of the launch, and if a starved request's kind (model x integrator) differs, whole
 // warps of other kinds vacate so they can switch.
 void build_lists(fpt_engine *e) {
-    int cnt[kNumKinds] = {0, 0, 0, 0};
+    int cnt[kNumKinds] = {};
     int active = 0;
     for (int s = 0; s < e->maxr; ++s) {
         e->h_preempt[s] = 0;
@@ -336,8 +336,8 @@ void build_lists(fpt_engine *e) {
             static_cast<int>(std::min<int64_t>(std::max<int64_t>(warps, 1), e->block / 32));
     }
     if (active < 2) return;
-    int64_t deficit[kNumKinds] = {0, 0, 0, 0};
-    bool over[kNumKinds] = {false, false, false, false};
+    int64_t deficit[kNumKinds] = {};
+    bool over[kNumKinds] = {};
     for (int s = 0; s < e->maxr; ++s) {
         if (!e->slot_req[s]) continue;
         Request &R = *e->reqs[e->slot_req[s]];

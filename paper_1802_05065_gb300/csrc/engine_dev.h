@@ -18,9 +18,9 @@ namespace fpt {
 
 enum : int { kSlotFree = 0, kSlotActive = 1, kSlotFinished = 2, kSlotCancelled = 3 };
 
-// Code paths a warp can run: kind = model + 2 x integrator (underdamped / overdamped x
-// Euler-Maruyama / Heun).  A warp runs one kind at a time.
-constexpr int kNumKinds = 4;
+// Code paths a warp can run: kind = model + 2 x integrator + 4 x ramp (underdamped / overdamped
+// x Euler-Maruyama / Heun x constant / ramped bias).  A warp runs one kind at a time.
+constexpr int kNumKinds = 8;
 
 // Philox blocks (of 4 steps) between re-bases of a trajectory's single-precision bias: gamma_k is
 // formed as gs + nu dt (s + 1) with gs = gb + nu dt Jf and gb = gamma0 + nu dt 4 c_base in FP64,
@@ -45,7 +45,7 @@ struct IdBlockAcc {
 struct SlotDev {
     // single-precision step constants
     float dt, A, amp, bmc, nudt, v0, r0, eb0;
-    int32_t w0, kind;         // kind = model + 2 x integrator
+    int32_t w0, kind;         // kind = model + 2 x integrator + 4 x ramp
     uint32_t key0, key1;
     // trajectories and budget
     uint64_t traj_offset, n_traj, max_steps, nblocks;   // nblocks = ceil(max_steps / 4)

@@ -15,10 +15,11 @@
 // resumes it exactly.  The ramped bias is formed from the trajectory's own step count, so a
 // trajectory's arithmetic never depends on which lane, launch or schedule ran it.
 //
-// A warp integrates one kind at a time (model x integrator: four code paths); the request of
-// each lane is free, so requests of the same kind share warps.  Refill is round-robin over
-// the claimable requests with a fair-share cap on in-flight lanes per request (first pass),
-// then without cap (second pass), so no lane idles while any request has work.
+// A warp integrates one kind at a time (model x integrator x constant or ramped bias: eight
+// code paths); the request of each lane is free, so requests of the same kind share warps.
+// Refill is round-robin over the claimable requests with a fair-share cap on in-flight lanes
+// per request (first pass), then without cap (second pass), so no lane idles while any request
+// has work.
 #include <cstdint>
 
 #include "engine_dev.h"
@@ -38,8 +39,7 @@ struct Lane {
     unsigned budget;      // blocks to the next event: step budget end, bias re-base, carry
     float gb, Jf;         // bias base and 4 x blocks since the base (exact)
     float dt, A, amp, bmc, nudt;
-    unsigned k0, k1;
-    PhiloxKeys K;         // round keys of the request's seed
+    PhiloxLane P;         // the trajectory's Philox stream (round keys, round-0 constants)
 };
 
 __device__ __forceinline__ float qnan_f() { return __int_as_float(0x7FFFFFFF); }
@@ -57,22 +57,20 @@ __device__ __forceinline__ void set_idle(Lane &L) {
     L.esc = -1;
     L.budget = 0xFFFFFFFFu;
     L.dt = L.A = L.amp = L.bmc = L.nudt = L.gb = L.Jf = 0.0f;
-    L.k0 = L.k1 = 0;
 }
 
 __device__ __forceinline__ unsigned clamp_u32(unsigned long long x) {
     return x > 0xFFFFFFFFull ? 0xFFFFFFFFu : static_cast<unsigned>(x);
 }
 
+// Request constants and the trajectory's Philox stream; gid and the block count c are set.
 __device__ __forceinline__ void load_consts(Lane &L, const SlotDev *S) {
     L.dt = S->dt;
     L.A = S->A;
     L.amp = S->amp;
     L.bmc = S->bmc;
     L.nudt = S->nudt;
-    L.k0 = S->key0;
-    L.k1 = S->key1;
-    philox_keys(L.K, L.k0, L.k1);
+    philox_lane_init(L.P, S->key0, S->key1, L.c_hi, L.gid_lo, L.gid_hi);
 }
 
 __device__ __forceinline__ unsigned long long lane_c(const Lane &L) {
@@ -320,9 +318,10 @@ __device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, int kin
     }
 }
 
-// Integrate blocks of kBlockSteps steps with model M and integrator H until the launch's block
-// count is reached or the whole warp has run out of work.  Returns the next block index.
-template <int M, int H, int T>
+// Integrate blocks of kBlockSteps steps with model M, integrator H and bias kind R (constant or
+// ramped) until the launch's block count is reached or the whole warp has run out of work.
+// Returns the next block index.
+template <int M, int H, int R, int T>
 __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E, unsigned b, int &n_active,
                                unsigned &cursor, unsigned long long &useful, unsigned &n_esc,
                                unsigned &n_cens) {
@@ -335,8 +334,7 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
         for (int t = 0; t < T; ++t) {
 #pragma unroll
             for (int h = 0; h < kBlockPhilox; ++h) {
-                const uint4 x = philox4x32_10k(
-                    make_uint4(L[t].c_lo + h, L[t].c_hi, L[t].gid_lo, L[t].gid_hi), L[t].K);
+                const uint4 x = philox_lane_block(L[t].P, L[t].c_lo, static_cast<unsigned>(h));
                 bm_pair_f32(x.x, x.y, L[t].bmc, rr[t][2 * h], tg[t][4 * h], tg[t][4 * h + 1]);
                 bm_pair_f32(x.z, x.w, L[t].bmc, rr[t][2 * h + 1], tg[t][4 * h + 2], tg[t][4 * h + 3]);
             }
@@ -357,10 +355,8 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
         for (int s = 0; s < kBlockSteps; ++s) {
 #pragma unroll
             for (int t = 0; t < T; ++t) {
-                step_f32<M, H>(L[t].r, L[t].v, rr[t][s >> 1], tg[t][s],
-                               fmaf(gsl[t], static_cast<float>(s), gs[t]),
-                               fmaf(gsl[t], static_cast<float>(s) + kBiasEnd<H>, gs[t]),
-                               L[t].dt, L[t].A, L[t].amp);
+                step_f32<M, H>(L[t].r, L[t].v, rr[t][s >> 1], tg[t][s], bias_b0<H, R>(gs[t], gsl[t], s),
+                               bias_b1<H, R>(gs[t], gsl[t], s), L[t].dt, L[t].A, L[t].amp);
                 mx[t] = fmaxf(mx[t], L[t].r);
             }
         }
@@ -385,17 +381,19 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
 #pragma unroll
                     for (int s = 0; s < kBlockSteps; ++s) {
                         step_f32<M, H>(L[t].r, L[t].v, rr[t][s >> 1], tg[t][s],
-                                       fmaf(gsl[t], static_cast<float>(s), gs[t]),
-                                       fmaf(gsl[t], static_cast<float>(s) + kBiasEnd<H>, gs[t]),
+                                       bias_b0<H, R>(gs[t], gsl[t], s), bias_b1<H, R>(gs[t], gsl[t], s),
                                        L[t].dt, L[t].A, L[t].amp);
                         if (L[t].r >= L[t].hb) phase_event(L[t], E, s);
                     }
                 }
                 if (L[t].r < -kPiF) wrap_down(L[t], E);
-                if (L[t].slot >= 0 && L[t].c_lo == 0u) L[t].c_hi += 1u;   // 2^32-block carry
+                if (L[t].slot >= 0 && L[t].c_lo == 0u) {   // 2^32-block carry
+                    L[t].c_hi += 1u;
+                    philox_lane_set_hi(L[t].P, L[t].c_hi - 1u, L[t].c_hi);
+                }
             }
             finish_lanes(L, E, useful, n_active, n_esc, n_cens);
-            refill(L, E, M + 2 * H, n_active, cursor);
+            refill(L, E, kind_of(M, H, R), n_active, cursor);
             if (!__any_sync(kFull, n_active > 0)) break;
         }
     }
@@ -459,18 +457,21 @@ __global__ void __launch_bounds__(T == 1 ? 640 : 256, 1) engine_chunk_kernel(Eng
             if (kind < 0) break;
         }
         switch (kind) {
-        case kUnder + 2 * kEuler:
-            b = run_blocks<kUnder, kEuler, T>(L, E, b, n_active, cursor, useful, n_esc, n_cens);
-            break;
-        case kOver + 2 * kEuler:
-            b = run_blocks<kOver, kEuler, T>(L, E, b, n_active, cursor, useful, n_esc, n_cens);
-            break;
-        case kUnder + 2 * kHeun:
-            b = run_blocks<kUnder, kHeun, T>(L, E, b, n_active, cursor, useful, n_esc, n_cens);
-            break;
+#define FPT_KIND_CASE(M_, H_, R_)                                                              \
+    case kind_of(M_, H_, R_):                                                                \
+        b = run_blocks<M_, H_, R_, T>(L, E, b, n_active, cursor, useful, n_esc, n_cens);       \
+        break;
+        FPT_KIND_CASE(kUnder, kEuler, kConstBias)
+        FPT_KIND_CASE(kOver, kEuler, kConstBias)
+        FPT_KIND_CASE(kUnder, kHeun, kConstBias)
+        FPT_KIND_CASE(kOver, kHeun, kConstBias)
+        FPT_KIND_CASE(kUnder, kEuler, kRamp)
+        FPT_KIND_CASE(kOver, kEuler, kRamp)
+        FPT_KIND_CASE(kUnder, kHeun, kRamp)
         default:
-            b = run_blocks<kOver, kHeun, T>(L, E, b, n_active, cursor, useful, n_esc, n_cens);
+            b = run_blocks<kOver, kHeun, kRamp, T>(L, E, b, n_active, cursor, useful, n_esc, n_cens);
             break;
+#undef FPT_KIND_CASE
         }
         if (!__any_sync(kFull, n_active > 0)) kind = -1;
     }

@@ -1,6 +1,7 @@
 // fpt_device.cuh -- device primitives of the FPT hot path (sm_103a).
 //
 //   philox4x32_10   counter-based generator (Salmon et al., SC'11), all in registers
+//   PhiloxLane      the same generator with round 0's block-independent half kept per lane
 //   bm_pair_f32     Box-Muller (Sec. III.B, nrand) in single precision, noise-scaled
 //   bm_pair_f64     Box-Muller in double precision, same arithmetic order as the FP64 oracle
 //   step_f32<M,H>   one Euler-Maruyama step of Alg. 1 / Alg. 3 (H = 0) or one stochastic Heun
@@ -25,28 +26,46 @@ constexpr float kPiF = 3.14159265358979323846f;
 
 constexpr float kTwoPiF = 6.28318530717958647692f;
 
-// Round keys of Philox4x32-10 for one key: k_r = k + r W (mod 2^32), r = 0..9.  A lane that
-// keeps them in registers spends no instruction on the key schedule per call.
-struct PhiloxKeys {
-    uint32_t a[10], b[10];
+// Philox4x32-10 of one trajectory, prepared for the many blocks it draws.  Counter words
+// (c0, c1, c2, c3) = (block lo, block hi, trajectory lo, trajectory hi): round 0 multiplies c2
+// by M1 and c0 by M0, so its outputs x' = hi(M1 c2) ^ c1 ^ k0, y' = lo(M1 c2) and the mask
+// c3 ^ k1 of z' = hi(M0 c0) ^ c3 ^ k1 are the same for every block that shares the high word.
+// They are kept per lane with the round keys of rounds 1..9; a block then costs one wide
+// multiply less per call.  Same output as philox4x32_10.
+struct PhiloxLane {
+    uint32_t ka[9], kb[9];    // round keys k + r W, rounds 1..9
+    uint32_t x0, y0, w1;      // round-0 outputs x', y' and the mask c3 ^ k1
 };
 
-__device__ __forceinline__ void philox_keys(PhiloxKeys &K, uint32_t k0, uint32_t k1) {
+__device__ __forceinline__ void philox_lane_init(PhiloxLane &P, uint32_t k0, uint32_t k1,
+                                                 uint32_t c_hi, uint32_t t_lo, uint32_t t_hi) {
 #pragma unroll
-    for (int r = 0; r < 10; ++r) {
-        K.a[r] = k0 + static_cast<uint32_t>(r) * kPhiloxW0;
-        K.b[r] = k1 + static_cast<uint32_t>(r) * kPhiloxW1;
+    for (int r = 1; r < 10; ++r) {
+        P.ka[r - 1] = k0 + static_cast<uint32_t>(r) * kPhiloxW0;
+        P.kb[r - 1] = k1 + static_cast<uint32_t>(r) * kPhiloxW1;
     }
+    const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * t_lo;
+    P.x0 = static_cast<uint32_t>(p1 >> 32) ^ c_hi ^ k0;
+    P.y0 = static_cast<uint32_t>(p1);
+    P.w1 = t_hi ^ k1;
 }
 
-// Philox4x32-10 with precomputed round keys (same output as philox4x32_10 below).
-__device__ __forceinline__ uint4 philox4x32_10k(uint4 c, const PhiloxKeys &K) {
+// The high counter word changed from old_hi to new_hi (a carry of the block count).
+__device__ __forceinline__ void philox_lane_set_hi(PhiloxLane &P, uint32_t old_hi, uint32_t new_hi) {
+    P.x0 ^= old_hi ^ new_hi;
+}
+
+// Words of block c_lo + h for h < 4 with c_lo a multiple of 4 (no carry into the high word):
+// round 0's product M0 (c_lo + h) is formed as the wide multiply-add M0 c_lo + M0 h.
+__device__ __forceinline__ uint4 philox_lane_block(const PhiloxLane &P, uint32_t c_lo, uint32_t h) {
+    const uint64_t p0 = static_cast<uint64_t>(kPhiloxM0) * c_lo + static_cast<uint64_t>(kPhiloxM0) * h;
+    uint4 c = make_uint4(P.x0, P.y0, static_cast<uint32_t>(p0 >> 32) ^ P.w1, static_cast<uint32_t>(p0));
 #pragma unroll
-    for (int round = 0; round < 10; ++round) {
-        const uint64_t p0 = static_cast<uint64_t>(kPhiloxM0) * c.x;
-        const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * c.z;
-        c = make_uint4(static_cast<uint32_t>(p1 >> 32) ^ c.y ^ K.a[round], static_cast<uint32_t>(p1),
-                       static_cast<uint32_t>(p0 >> 32) ^ c.w ^ K.b[round], static_cast<uint32_t>(p0));
+    for (int round = 1; round < 10; ++round) {
+        const uint64_t q0 = static_cast<uint64_t>(kPhiloxM0) * c.x;
+        const uint64_t q1 = static_cast<uint64_t>(kPhiloxM1) * c.z;
+        c = make_uint4(static_cast<uint32_t>(q1 >> 32) ^ c.y ^ P.ka[round - 1], static_cast<uint32_t>(q1),
+                       static_cast<uint32_t>(q0 >> 32) ^ c.w ^ P.kb[round - 1], static_cast<uint32_t>(q0));
     }
     return c;
 }
@@ -123,6 +142,12 @@ struct StepConstF32 {
 
 enum : int { kUnder = 0, kOver = 1 };
 enum : int { kEuler = 0, kHeun = 1 };
+enum : int { kConstBias = 0, kRamp = 1 };
+
+// Code path of a request: kind = model + 2 integrator + 4 ramp (eight paths).
+__host__ __device__ constexpr int kind_of(int model, int integrator, int ramp) {
+    return model + 2 * integrator + 4 * ramp;
+}
 
 // Bias arguments of the steps of a block.  Every FP32 step takes its bias already multiplied by
 // dt, so bias and noise form addends that do not depend on the state (off the step's serial
@@ -136,6 +161,21 @@ constexpr float kBiasEnd = H == kHeun ? 0.5f : 1.0f;
 __device__ __forceinline__ void bias_line(float gs, float nudt, float dt, float &base, float &slope) {
     base = __fmul_rn(dt, gs);
     slope = __fmul_rn(dt, nudt);
+}
+
+// Step s's bias arguments.  R = 1: the ramp of Alg. 3 (the line above).  R = 0: a constant bias
+// (nu dt rounds to a zero slope), where both arguments are the base itself -- the value the
+// line gives there (0 s + base = base), without the per-step multiply-add.  Every FP32 kernel
+// selects R the same way (the ramp flag of the request's kind), so they agree bit for bit.
+template <int H, int R>
+__device__ __forceinline__ float bias_b0(float base, float slope, int s) {
+    if constexpr (R) return fmaf(slope, static_cast<float>(s), base);
+    else return base;
+}
+template <int H, int R>
+__device__ __forceinline__ float bias_b1(float base, float slope, int s) {
+    if constexpr (R) return fmaf(slope, static_cast<float>(s) + kBiasEnd<H>, base);
+    else return base;
 }
 
 // One step with noise increment sigma z = rr * trig and dt-scaled bias b0, b1 (see bias_line);

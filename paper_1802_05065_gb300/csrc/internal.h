@@ -32,7 +32,7 @@ constexpr int kMaxBins = 1 << 20;
 struct Decoded {
     int model = 0, output = 0;
     int integrator = 0;  // FPT_EULER_MARUYAMA | FPT_HEUN
-    int kind = 0;        // model + 2 integrator: the code path a warp runs
+    int kind = 0;        // model + 2 integrator + 4 ramp (nudt_f != 0): the FP32 code path
     double alpha = 0, D = 0, gamma0 = 0, nudt = 0, amp = 1, dt = 0, sigma = 0;
     double phi0 = 0, v0 = 0, th = 0;
     uint64_t max_steps = 0;
@@ -61,7 +61,7 @@ void sums_to_result(const Decoded &d, const fpt_sums &s, fpt_result *out);
 
 // ---- kernels (launch wrappers; definitions in plain.cu / engine_kernels.cu) ----
 struct PlainArgs {
-    int model, integrator;
+    int model, integrator, kind;
     uint32_t key0, key1;
     uint64_t traj0, n;
     int64_t *steps;

@@ -92,7 +92,7 @@ __device__ __forceinline__ void nl_claim(NLane &L, const NoAllocArgs &a, unsigne
     }
 }
 
-template <int M, int H>
+template <int M, int H, int R>
 __global__ void __launch_bounds__(kBlock) noalloc_kernel(NoAllocArgs a) {
     extern __shared__ unsigned int sh_hist[];
     __shared__ unsigned long long sh_sums[8];   // done, escaped, s1 lo/hi, s2 lo/hi, under, over
@@ -131,8 +131,8 @@ __global__ void __launch_bounds__(kBlock) noalloc_kernel(NoAllocArgs a) {
         bias_line(fmaf(a.nudt, L.Jf, L.gb), a.nudt, a.dt, gs, gsl);
 #pragma unroll
         for (int s = 0; s < kBlockSteps; ++s) {
-            step_f32<M, H>(L.r, L.v, rr[s >> 1], tg[s], fmaf(gsl, static_cast<float>(s), gs),
-                           fmaf(gsl, static_cast<float>(s) + kBiasEnd<H>, gs), a.dt, a.A, a.amp);
+            step_f32<M, H>(L.r, L.v, rr[s >> 1], tg[s], bias_b0<H, R>(gs, gsl, s),
+                           bias_b1<H, R>(gs, gsl, s), a.dt, a.A, a.amp);
             if (L.r >= L.hb) {
                 const float eb = fmaf(-kTwoPiF, static_cast<float>(L.w - a.w0), a.eb0);
                 if (L.r >= eb) {
@@ -309,10 +309,20 @@ extern "C" fpt_status fpt_run_noalloc(const fpt_params *params, uint64_t n_traj,
         set_error("fpt_run_noalloc: hist_bins must be <= 10240 (per-CTA histogram in shared memory)");
         return FPT_EINVAL;
     }
-    void (*kernel)(NoAllocArgs) = d.kind == kUnder     ? noalloc_kernel<kUnder, kEuler>
-                                  : d.kind == kOver      ? noalloc_kernel<kOver, kEuler>
-                                  : d.kind == kUnder + 2 ? noalloc_kernel<kUnder, kHeun>
-                                                         : noalloc_kernel<kOver, kHeun>;
+    void (*kernel)(NoAllocArgs) = nullptr;
+    switch (d.kind) {
+#define FPT_KIND_CASE(M_, H_, R_) \
+    case kind_of(M_, H_, R_): kernel = noalloc_kernel<M_, H_, R_>; break;
+    FPT_KIND_CASE(kUnder, kEuler, kConstBias)
+    FPT_KIND_CASE(kOver, kEuler, kConstBias)
+    FPT_KIND_CASE(kUnder, kHeun, kConstBias)
+    FPT_KIND_CASE(kOver, kHeun, kConstBias)
+    FPT_KIND_CASE(kUnder, kEuler, kRamp)
+    FPT_KIND_CASE(kOver, kEuler, kRamp)
+    FPT_KIND_CASE(kUnder, kHeun, kRamp)
+#undef FPT_KIND_CASE
+    default: kernel = noalloc_kernel<kOver, kHeun, kRamp>; break;
+    }
     if (e == cudaSuccess)
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kBlock, shmem);
     if (e != cudaSuccess) {

@@ -87,7 +87,7 @@ done:
 // threshold in the current cell's coordinates; hb = min(eb, pi) is the one bound tested every
 // step; the lower wrap at -pi is applied at the ends of blocks of kBlockSteps steps, as in the
 // engine.
-template <int M, int H>
+template <int M, int H, int R>
 __global__ void __launch_bounds__(256) plain_f32_kernel(PlainArgs a) {
     const uint64_t i = static_cast<uint64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= a.n) return;
@@ -118,9 +118,8 @@ __global__ void __launch_bounds__(256) plain_f32_kernel(PlainArgs a) {
             bias_line(fmaf(a.nudt_f, Jf, gb), a.nudt_f, a.dt_f, gs, gsl);
 #pragma unroll
             for (int s = 0; s < kBlockSteps; ++s) {
-                step_f32<M, H>(r, v, rr[s >> 1], tg[s], fmaf(gsl, static_cast<float>(s), gs),
-                               fmaf(gsl, static_cast<float>(s) + kBiasEnd<H>, gs), a.dt_f, a.A_f,
-                               a.amp_f);
+                step_f32<M, H>(r, v, rr[s >> 1], tg[s], bias_b0<H, R>(gs, gsl, s),
+                               bias_b1<H, R>(gs, gsl, s), a.dt_f, a.A_f, a.amp_f);
                 if (r >= hb) {
                     // threshold in the current cell: eb = phi* - 2 pi w (same rounding as the engine)
                     const float eb = fmaf(-kTwoPiF, static_cast<float>(w - a.w0), a.eb0_f);
@@ -274,11 +273,18 @@ cudaError_t launch_plain_f64(const PlainArgs &a, cudaStream_t s) {
 cudaError_t launch_plain_f32(const PlainArgs &a, cudaStream_t s) {
     const unsigned block = 256;
     const unsigned grid = grid_for(a.n, block);
-    switch (a.model + 2 * a.integrator) {
-    case kUnder: plain_f32_kernel<kUnder, kEuler><<<grid, block, 0, s>>>(a); break;
-    case kOver: plain_f32_kernel<kOver, kEuler><<<grid, block, 0, s>>>(a); break;
-    case kUnder + 2: plain_f32_kernel<kUnder, kHeun><<<grid, block, 0, s>>>(a); break;
-    default: plain_f32_kernel<kOver, kHeun><<<grid, block, 0, s>>>(a); break;
+    switch (a.kind) {
+#define FPT_KIND_CASE(M_, H_, R_) \
+    case kind_of(M_, H_, R_): plain_f32_kernel<M_, H_, R_><<<grid, block, 0, s>>>(a); break;
+    FPT_KIND_CASE(kUnder, kEuler, kConstBias)
+    FPT_KIND_CASE(kOver, kEuler, kConstBias)
+    FPT_KIND_CASE(kUnder, kHeun, kConstBias)
+    FPT_KIND_CASE(kOver, kHeun, kConstBias)
+    FPT_KIND_CASE(kUnder, kEuler, kRamp)
+    FPT_KIND_CASE(kOver, kEuler, kRamp)
+    FPT_KIND_CASE(kUnder, kHeun, kRamp)
+#undef FPT_KIND_CASE
+    default: plain_f32_kernel<kOver, kHeun, kRamp><<<grid, block, 0, s>>>(a); break;
     }
     return cudaGetLastError();
 }
@@ -345,6 +351,7 @@ extern "C" fpt_status fpt_plain_launch(const fpt_params *params, uint64_t seed, 
     std::memset(&a, 0, sizeof(a));
     a.model = d.model;
     a.integrator = d.integrator;
+    a.kind = d.kind;
     a.key0 = static_cast<uint32_t>(seed);
     a.key1 = static_cast<uint32_t>(seed >> 32);
     a.traj0 = traj0;
