@@ -19,13 +19,16 @@ timed region are summarised.  Under torchrun every rank runs its own engine on i
 ids (weak scaling); the reported value sums all ranks' steps and divides by the slowest rank's
 time.
 
-Further fields of the one JSON line: `roofline` (XU-pipe bound of the resident kernel, ncu
-traffic per launch), `e2e` (a fresh engine driven through the C ABI from host memory),
-`fp64_plain` (the one-trajectory-per-thread FP64 kernel on the same GPU, its FP32 twin and a
-library FP64 GEMM rate for context), `fp32_engine_point` (accuracy of the engine on one point),
-`heun` (the same sweep with the stochastic Heun integrator), `other_workloads` (the ramp sweep
-and the 256-set uneven batch), `autotune`, `serving` (Poisson request stream: p50 / p99
-latency), `cpu_baseline` (the FP64 oracle on the host cores, a bounded sample), `clocks`.
+Further fields of the one JSON line: `roofline` (XU-pipe bound of the resident kernel, with the
+issue bound at the measured instructions per step; ncu traffic per launch), `e2e` (a fresh
+engine driven through the C ABI from host memory), `fp64_equal_accuracy` (the plain
+one-trajectory-per-thread FP64 kernel against the FP32 engine on one point: the same trajectory
+ids, and both to the same relative standard error), `heun` (the same sweep with the stochastic
+Heun integrator), `other_workloads` (the ramp sweep, the 256-set uneven batch, the Fig. 10b
+junction, time to solution against N_r), `autotune`, `serving` (Poisson request streams at the
+specified rate and at 0.9x / 0.5x capacity: offered load, p50 / p99 latency and slowdown, FP32
+results against FP64 on sampled requests), `cpu_baseline` (the FP64 oracle on the host cores, a
+bounded sample), `clocks`.
 
 --impl reference times the FP64 CPU oracle (the method's plain restatement) on the host cores
 on a bounded sample of the same workload.
@@ -63,6 +66,7 @@ def parse():
     ap.add_argument("--chunk-steps", type=int, default=65536)
     ap.add_argument("--traj-per-thread", type=int, default=1)
     ap.add_argument("--block", type=int, default=640)
+    ap.add_argument("--blocks-per-sm", type=int, default=0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
@@ -74,7 +78,7 @@ def parse():
                     help="skip the ramp-sweep and uneven-batch throughput legs")
     ap.add_argument("--no-autotune", action="store_true",
                     help="use --traj-per-thread / --block as given instead of the autotuner's choice")
-    ap.add_argument("--serving-requests", type=int, default=100)
+    ap.add_argument("--serving-requests", type=int, default=60)
     return ap.parse_args()
 
 
@@ -244,6 +248,9 @@ def run_reference(args):
 # read and written once per launch, whatever the number of steps, so a 65 536-step launch moves
 # the same bytes as the captured 4096-step one.
 TRAFFIC_BYTES_PER_LAUNCH = 3.63e6
+# warp instructions x 32 / lane-steps of the same capture (smsp__inst_executed): the issue bound
+# of the current kernel is 4 schedulers x 32 lanes x N_SM x f / this
+INSTRUCTIONS_PER_STEP = 22.78
 
 
 def roofline_model(n_sm: int, f_mhz: float):
@@ -255,6 +262,148 @@ def roofline_model(n_sm: int, f_mhz: float):
     xu_per_step = 3.0
     xu_rate = 16.0
     return xu_rate * n_sm * f_mhz * 1e6 / xu_per_step, xu_per_step, xu_rate
+
+
+def fp64_equal_accuracy(pkg, torch, dev, point, block, T, bps):
+    """The FP32 persistent engine against the plain one-trajectory-per-thread FP64 kernel on one
+    point (Alg. 1 structure, every operation in double precision), at equal accuracy:
+      same_ids: both integrate the same 2^20 trajectory ids of the same seed, so their means
+                carry the same statistical error; time to solution, trajectory-steps/s, mean and
+                SEM of each, and the per-trajectory difference of the escape times (FP32 - FP64);
+      same_sem: the engine runs with a 0.1 % relative-standard-error stop rule (prefix of whole
+                id blocks) and the FP64 kernel integrates exactly the prefix the engine kept.
+    Times: FP64 = CUDA events around kernel + exact reduction; FP32 = wall time from submission
+    to the finished result through the engine's public API (admission, launches, completion
+    scan, read-back)."""
+    import numpy as np
+    import workloads
+    from paper_1802_05065_gb300 import api
+    d32 = workloads.scaled(point)
+    d64 = workloads.scaled(point, precision="fp64")
+    seed, n = point["seed"], 2**20
+
+    def plain64(count):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        st = api.run_plain(d64, count, seed)
+        res, _, _ = api.reduce(d64, st)
+        b.record()
+        torch.cuda.synchronize()
+        return res, st, a.elapsed_time(b) / 1e3
+
+    def engine32(count, **over):
+        with pkg.Engine(dev, chunk_steps=16384, threads_per_block=block, traj_per_thread=T,
+                        blocks_per_sm=bps) as eng:
+            eng.wait(eng.submit(pkg.params_from(d32), 4096, seed + 1), 60.0)   # warm-up
+            torch.cuda.synchronize()
+            c0 = eng.counters()
+            t0 = time.perf_counter()
+            rid = eng.submit(pkg.params_from(d32, **over), count, seed)
+            res = eng.wait(rid, 600.0)
+            el = time.perf_counter() - t0
+            c1 = eng.counters()
+            steps = eng.per_traj_steps(rid, count) if over.get("keep_per_traj") else None
+        return res, el, c1["useful_steps"] - c0["useful_steps"], steps
+
+    plain64(4096)                                                 # warm-up
+    r64, st64, t64 = plain64(n)
+    r32, t32, w32, k32 = engine32(n, keep_per_traj=1)
+    k64 = st64.cpu().numpy()
+    both = (k32 >= 0) & (k64 >= 0)
+    diff = (k32[both] - k64[both]).astype(np.float64) * point["dt"]
+    rel = np.abs(k32[both] - k64[both]) / np.maximum(k64[both], 1)
+
+    def side(res, t, work):
+        return {"seconds": t, "steps_per_s": work / t, "mean_fpt": res.mean, "sem": res.sem,
+                "n": res.n_used}
+    same_ids = {"trajectories": n, "fp64_plain": side(r64, t64, r64.steps_total),
+                "fp32_engine": side(r32, t32, w32),
+                "time_ratio_fp64_over_fp32": t64 / t32,
+                "paired_mean_diff": float(np.mean(diff)),
+                "paired_diff_se": float(np.std(diff, ddof=1) / math.sqrt(diff.size)),
+                "paired_within_5pct": float(np.mean(rel <= 0.05))}
+    r32s, t32s, w32s, _ = engine32(n, stop_rse=1e-3)
+    r64s, _, t64s = plain64(int(r32s.n_used))
+    same_sem = {"target_rse": 1e-3, "trajectories": int(r32s.n_used),
+                "fp64_plain": side(r64s, t64s, r64s.steps_total),
+                "fp32_engine": side(r32s, t32s, w32s),
+                "time_ratio_fp64_over_fp32": t64s / t32s}
+    return {"point": "overdamped gamma=0.9 D=0.2 dt=1e-3, seed %d" % seed,
+            "same_ids": same_ids, "same_sem": same_sem}
+
+
+def serving_loads(pkg, dev, n_requests):
+    """Continuous batching under a Poisson stream of requests drawn as in the uneven batch
+    (2^12..2^20 trajectories, 1 % RSE stop rule), at three offered loads:
+      - the stream at 200 requests/s as specified, which offers far more work than one GPU
+        integrates (its latencies measure the drain of a backlog);
+      - the same requests with arrival times stretched so the offered load is 0.9x and 0.5x the
+        capacity, capacity = the engine's throughput on this mix while saturated.
+    Offered load = trajectory-steps the requests need, each measured alone in an idle engine,
+    / arrival span.  Slowdown = latency / the request's latency alone.  Four requests (the
+    cheapest ones) are also run by the plain FP64 kernel on the ids their FP32 result used."""
+    import workloads
+    from paper_1802_05065_gb300 import serving as _srv
+    chunk = 4096
+    stream = workloads.serving_stream(n_requests=n_requests)
+    alone = _srv.run_alone(stream, device=dev, chunk_steps=chunk)
+    lat_alone = [a["latency_s"] for a in alone]
+    work = float(sum(a["steps"] for a in alone))
+    span = stream[-1][0]
+
+    def one(st, label):
+        out = _srv.run_stream(st, device=dev, chunk_steps=chunk, timeout_s=600.0,
+                              keep_results=True)
+        res = out.pop("results")
+        lat = [r.latency_s for r in res if r is not None]
+        al = [la for la, r in zip(lat_alone, res) if r is not None]
+        same = sum(1 for a, r in zip(alone, res) if r is not None and
+                   (r.n_used, r.mean, r.var) == (a["result"].n_used, a["result"].mean,
+                                                 a["result"].var))
+        row = {"load": label, "rate_hz": len(st) / st[-1][0],
+               "offered_steps_per_s": work / st[-1][0], "requests": out["requests"],
+               "completed": out["completed"], "results_equal_alone": same,
+               "wall_s": out["wall_s"], "steps_per_s": out["steps_per_s"],
+               "escapes_per_s": out["escapes_per_s"]}
+        row.update(_srv.latency_summary(lat, al))
+        return row
+
+    sat = one(stream, "as specified: Poisson 200 requests/s")
+    capacity = sat["steps_per_s"]
+    sat["offered_over_capacity"] = sat["offered_steps_per_s"] / capacity
+    loads = [sat]
+    for x in (0.9, 0.5):
+        f = (work / span) / (x * capacity)
+        row = one(_srv.stretch(stream, f), f"{x} x capacity")
+        row["offered_over_capacity"] = row["offered_steps_per_s"] / capacity
+        loads.append(row)
+    # FP32 results against the plain FP64 kernel on the same trajectory ids (same prefix)
+    import torch
+    from paper_1802_05065_gb300 import api
+    picks = sorted(range(len(alone)), key=lambda i: alone[i]["steps"])[:4]
+    vs64 = []
+    for i in picks:
+        d = stream[i][1]
+        r32 = alone[i]["result"]
+        d64 = workloads.scaled(d, precision="fp64")
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        st = api.run_plain(d64, int(r32.n_used), int(d["seed"]))
+        r64, _, _ = api.reduce(d64, st)
+        b.record()
+        torch.cuda.synchronize()
+        z = (r32.mean - r64.mean) / math.sqrt(r32.sem ** 2 + r64.sem ** 2)
+        vs64.append({"request": i, "trajectories": int(r32.n_used), "fp32_mean": r32.mean,
+                     "fp32_sem": r32.sem, "fp64_mean": r64.mean, "fp64_sem": r64.sem,
+                     "z_combined_se": z, "fp32_alone_s": r32.latency_s,
+                     "fp64_plain_s": a.elapsed_time(b) / 1e3})
+    return {"stream": f"{n_requests} requests drawn as in the uneven batch, 2^12..2^20 "
+                      "trajectories, 1 % RSE stop rule, Poisson arrivals",
+            "chunk_steps": chunk, "capacity_steps_per_s": capacity,
+            "work_steps": work, "alone_total_s": sum(lat_alone), "loads": loads,
+            "fp32_vs_fp64": vs64}
 
 
 def run_ours(args):
@@ -288,8 +437,9 @@ def run_ours(args):
 
     n_traj = 2**20
     pts = workloads.overdamped_sweep(n_traj=n_traj)
-    # launch shape (trajectories per thread, threads per block) from the autotuner, measured on a
-    # short run of the same sweep; the chunk stays the bench's step (--chunk-steps)
+    # launch shape (trajectories per thread, threads per block, CTAs per SM) from the autotuner,
+    # measured on a short run of the same sweep over every shape the kernel can launch; the chunk
+    # stays the bench's step (--chunk-steps)
     tuned = None
     if not args.no_autotune:
         from paper_1802_05065_gb300 import autotune
@@ -297,8 +447,10 @@ def run_ours(args):
                               chunk=8192, save=False)
         args.traj_per_thread = tuned["best"]["traj_per_thread"]
         args.block = tuned["best"]["threads_per_block"]
+        args.blocks_per_sm = tuned["best"]["blocks_per_sm"]
     eng = pkg.Engine(local, chunk_steps=args.chunk_steps, traj_per_thread=args.traj_per_thread,
-                     threads_per_block=args.block)
+                     threads_per_block=args.block,
+                     blocks_per_sm=args.blocks_per_sm)
     stream = torch.cuda.ExternalStream(eng.stream, device=torch.device("cuda", local))
     rids = [eng.submit(pkg.params_from(d, traj_offset=rank * n_traj), n_traj, d["seed"])
             for d in pts]
@@ -330,15 +482,6 @@ def run_ours(args):
     barrier()
     torch.cuda.synchronize()
     c1 = eng.counters()
-    # accuracy of the FP32 engine on the gamma = 0.9, D = 0.2 point (finished after the timed
-    # region if it had not yet), beside the plain FP64 kernel's mean below
-    fast_point = None
-    try:
-        res_fast = eng.wait(rids[11], 120.0)
-        fast_point = {"mean_fpt": res_fast.mean, "sem": res_fast.sem, "n": res_fast.n_used,
-                      "point": "gamma=0.9 D=0.2, 2^20 trajectories, FP32 engine"}
-    except pkg.FptError:
-        pass
     ms = sum(a.elapsed_time(b) for a, b in evs)
     steps = c1["useful_steps"] - c0["useful_steps"]
     escapes = c1["escapes"] - c0["escapes"]
@@ -354,7 +497,8 @@ def run_ours(args):
     e2e = None
     if not args.no_e2e:
         eng2 = pkg.Engine(local, chunk_steps=args.chunk_steps,
-                          traj_per_thread=args.traj_per_thread, threads_per_block=args.block)
+                          traj_per_thread=args.traj_per_thread, threads_per_block=args.block,
+                     blocks_per_sm=args.blocks_per_sm)
         import ctypes
         from paper_1802_05065_gb300 import _lib
         params = [pkg.params_from(d, traj_offset=rank * n_traj) for d in pts]
@@ -386,54 +530,20 @@ def run_ours(args):
                "escapes_per_s": allreduce(cc["escapes"]) / el_max}
         eng2.close()
 
-    # plain FP64 baseline on the same GPU (one trajectory per thread, paper-literal FP64),
-    # gamma = 0.9, D = 0.2 point, 2^17 trajectories
+    # the plain one-trajectory-per-thread FP64 kernel (Alg. 1 structure, paper-literal FP64)
+    # against the FP32 engine at equal accuracy on the gamma = 0.9, D = 0.2 point
     fp64 = None
     if not args.no_fp64 and rank == 0:
-        from paper_1802_05065_gb300 import api
-        d = workloads.scaled(pts[11], precision="fp64", max_steps=10**8)
-        n64 = 2**17
-        api.run_plain(d, 1024, 3)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        st = api.run_plain(d, n64, d["seed"])
-        b.record()
-        torch.cuda.synchronize()
-        ms64 = a.elapsed_time(b)
-        res, _, _ = api.reduce(d, st)
-        fp64 = {"value": (res.steps_total) / (ms64 / 1e3), "unit": UNIT,
-                "fp32_engine_speedup": None,
-                "escapes_per_s": res.n_escaped / (ms64 / 1e3),
-                "sample": f"gamma=0.9 D=0.2 point, {n64} trajectories, one per thread, FP64",
-                "mean_fpt": res.mean, "sem": res.sem}
-        # FP32 plain kernel on the same sample (no refill), for the load-balance comparison
-        d32 = workloads.scaled(pts[11], max_steps=10**8)
-        a.record()
-        st = api.run_plain(d32, n64, d["seed"])
-        b.record()
-        torch.cuda.synchronize()
-        ms32 = a.elapsed_time(b)
-        res32, _, _ = api.reduce(d32, st)
-        fp64["fp32_plain_value"] = res32.steps_total / (ms32 / 1e3)
-        # the FP64 pipe of this GPU for context: a library DGEMM (cuBLAS) on 8192^2 operands
-        x = torch.randn(8192, 8192, dtype=torch.float64, device=torch.device("cuda", local))
-        torch.matmul(x, x)
-        torch.cuda.synchronize()
-        a.record()
-        for _ in range(3):
-            torch.matmul(x, x)
-        b.record()
-        torch.cuda.synchronize()
-        fp64["dgemm_tflops"] = 3 * 2 * 8192.0 ** 3 / (a.elapsed_time(b) / 1e3) / 1e12
-        del x
+        fp64 = fp64_equal_accuracy(pkg, torch, local, pts[11], args.block, args.traj_per_thread,
+                                   args.blocks_per_sm)
 
     # the same sweep with the stochastic Heun integrator (4 XU evaluations per step: two sin of
     # the predictor-corrector, half of the Box-Muller pair), a few engine iterations
     heun = None
     if not args.no_heun and rank == 0:
         eng3 = pkg.Engine(local, chunk_steps=args.chunk_steps,
-                          traj_per_thread=args.traj_per_thread, threads_per_block=args.block)
+                          traj_per_thread=args.traj_per_thread, threads_per_block=args.block,
+                     blocks_per_sm=args.blocks_per_sm)
         st3 = torch.cuda.ExternalStream(eng3.stream, device=torch.device("cuda", local))
         for d in pts:
             eng3.submit(pkg.params_from(workloads.scaled(d, integrator="heun")), n_traj,
@@ -466,7 +576,8 @@ def run_ours(args):
     # trajectories per set, constant and ramped, lengths 10^3..10^8 steps) in one engine
     def _leg(reqs, iters, chunk):
         e4 = pkg.Engine(local, chunk_steps=chunk, traj_per_thread=args.traj_per_thread,
-                        threads_per_block=args.block)
+                        threads_per_block=args.block,
+                     blocks_per_sm=args.blocks_per_sm)
         s4 = torch.cuda.ExternalStream(e4.stream, device=torch.device("cuda", local))
         for d, n, sd in reqs:
             e4.submit(pkg.params_from(d), n, sd)
@@ -509,7 +620,7 @@ def run_ours(args):
         # to completion; below the lane count the longest trajectories set the time (App. A)
         tts = []
         with pkg.Engine(local, chunk_steps=16384, traj_per_thread=args.traj_per_thread,
-                        threads_per_block=args.block) as e5:
+                        threads_per_block=args.block, blocks_per_sm=args.blocks_per_sm) as e5:
             lanes5 = e5.counters()["lanes"]
             for lg in (12, 14, 16, 18, 20, 22):
                 b0 = e5.counters()
@@ -526,15 +637,7 @@ def run_ours(args):
 
     serving = None
     if not args.no_serving and rank == 0 and world == 1:
-        from paper_1802_05065_gb300 import serving as _srv
-        sv = _srv.run_stream(workloads.serving_stream(n_requests=args.serving_requests),
-                             device=local, chunk_steps=4096, timeout_s=240.0)
-        serving = {"p50_latency_s": sv["p50_s"], "p99_latency_s": sv["p99_s"],
-                   "mean_latency_s": sv["mean_s"], "requests": sv["requests"],
-                   "completed": sv["completed"], "wall_s": sv["wall_s"],
-                   "steps_per_s": sv["steps_per_s"], "escapes_per_s": sv["escapes_per_s"],
-                   "stream": f"{args.serving_requests} requests, Poisson 200/s, uneven-batch "
-                             "parameters, 2^12..2^20 trajectories, 1 % RSE stop rule"}
+        serving = serving_loads(pkg, local, args.serving_requests)
 
     cpu = None
     if not args.no_cpu_baseline and rank == 0 and world == 1:
@@ -561,10 +664,17 @@ def run_ours(args):
             "traffic": TRAFFIC_BYTES_PER_LAUNCH, "traffic_unit": "bytes per launch (lane state)",
             "pipe": "xu", "xu_ops_per_step": xu_step, "xu_ops_per_clk_per_sm": xu_rate,
             "sm_count": n_sm, "clock_mhz": f_max,
+            "issue_bound": {
+                "instructions_per_step": INSTRUCTIONS_PER_STEP,
+                "peak": 128.0 * n_sm * f_max * 1e6 / INSTRUCTIONS_PER_STEP / 1e9,
+                "frac": (kern_steps_s / (128.0 * n_sm * f_max * 1e6 / INSTRUCTIONS_PER_STEP))
+                if kern_steps_s else None,
+                "source": "instructions per step from ncu smsp__inst_executed (small capture, "
+                          "profiles/engine_chunk_kernel__overdamped_sweep.md)"},
             "note": "achieved = useful steps / summed resident-kernel event time; peak = "
-                    "16 XU ops/clk/SM x N_SM x max SM clock / 3 XU ops per step"}
-    if fp64:
-        fp64["fp32_engine_speedup"] = per_gpu_steps_s / fp64["value"]
+                    "16 XU ops/clk/SM x N_SM x max SM clock / 3 XU ops per step (the method's "
+                    "transcendentals: sin of the step, half of the Box-Muller log2, sqrt, sin, "
+                    "cos)"}
     if heun and heun["kernel_gstep_s"]:
         hpeak = 16.0 * n_sm * f_max * 1e6 / 4.0
         heun["roofline"] = {"bound": "alu", "achieved": heun["kernel_gstep_s"],
@@ -589,12 +699,16 @@ def run_ours(args):
         "roofline": roof,
         "cpu_baseline": cpu,
         "e2e": e2e,
-        "fp64_plain": fp64,
-        "fp32_engine_point": fast_point,
+        "fp64_equal_accuracy": fp64,
         "heun": heun,
         "other_workloads": mix,
         "autotune": None if not tuned else {
             "best": tuned["best"], "chunk_for_2pct_overhead": tuned["chunk_steps"],
+            "chunk_used": args.chunk_steps,
+            "chunk_note": "the timed loop keeps --chunk-steps so that one step is a long launch "
+                          "whose fixed cost (graph launch, scan, status copy) is negligible; the "
+                          "tuner's chunk is the shortest with <= 2 % host overhead, for "
+                          "latency-sensitive use",
             "trials": [{"cfg": t["cfg"], "gstep_s": round(t["steps_per_s_kernel"] / 1e9, 1)}
                        for t in tuned["trials"]]},
         "serving": serving,

@@ -214,6 +214,15 @@ fpt_status fpt_release(fpt_engine *e, uint64_t req_id);
 
 fpt_status fpt_get_counters(fpt_engine *e, fpt_engine_counters *out);
 
+/* Launch shapes of the resident kernel: *blocks_per_sm receives how many CTAs of
+ * threads_per_block threads (each integrating traj_per_thread trajectories) fit on one SM of
+ * the current device, 0 when the kernel cannot launch with that shape (threads_per_block not a
+ * multiple of 32, or above 640 for one trajectory per thread / 256 for two).  For autotuners:
+ * fpt_engine_config.blocks_per_sm may be 1 .. this value.  FPT_EINVAL for traj_per_thread
+ * other than 1 or 2; FPT_ECUDA if the occupancy query fails (no device). */
+fpt_status fpt_engine_occupancy(int32_t traj_per_thread, int32_t threads_per_block,
+                                int32_t *blocks_per_sm);
+
 /* CUDA stream the engine runs on (cudaStream_t as void*). */
 void *fpt_engine_stream(fpt_engine *e);
 

@@ -5,7 +5,7 @@ friendly helpers (device buffers and streams from PyTorch).  No computation of t
 in Python.
 """
 from ._lib import (  # noqa: F401
-    Engine, FptError, Params, Result, Sums, load, normals_fill, params_from, philox_fill,
+    Engine, FptError, Params, Result, Sums, engine_occupancy, load, normals_fill, params_from, philox_fill,
     plain_launch, reduce_steps, run_noalloc, sums_finish, version,
     UNDERDAMPED, OVERDAMPED, FP32, FP64, EULER_MARUYAMA, HEUN, OUT_TIME, OUT_BIAS, TH_ABSOLUTE, TH_FROM_START,
 )

@@ -91,6 +91,7 @@ EXPORTS = [
     "fpt_release", "fpt_get_counters", "fpt_engine_stream", "fpt_destroy", "fpt_last_error",
     "fpt_status_string", "fpt_philox_fill", "fpt_normals_fill", "fpt_version",
     "fpt_request_sums", "fpt_run_noalloc", "fpt_checkpoint", "fpt_restore",
+    "fpt_engine_occupancy",
 ]
 
 _lib = None
@@ -134,11 +135,12 @@ def load() -> ctypes.CDLL:
     L.fpt_philox_fill.argtypes = [u64, u64, u64, u64, vp, vp]
     L.fpt_normals_fill.argtypes = [i32, u64, u64, u64, u64, vp, vp]
     L.fpt_version.restype = ctypes.c_char_p
+    L.fpt_engine_occupancy.argtypes = [i32, i32, P(ctypes.c_int32)]
     for name in ("fpt_plain_launch", "fpt_reduce_steps", "fpt_sums_finish", "fpt_create",
                  "fpt_submit", "fpt_step", "fpt_poll", "fpt_wait", "fpt_histogram",
                  "fpt_per_traj", "fpt_per_traj_steps", "fpt_release", "fpt_get_counters",
                  "fpt_destroy", "fpt_philox_fill", "fpt_normals_fill", "fpt_request_sums",
-                 "fpt_run_noalloc", "fpt_checkpoint", "fpt_restore"):
+                 "fpt_run_noalloc", "fpt_checkpoint", "fpt_restore", "fpt_engine_occupancy"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L
@@ -208,6 +210,13 @@ def run_noalloc(p: Params, n_traj: int, seed: int, d_steps: int, d_sums: int, d_
                 stream: int = 0):
     """fpt_run_noalloc: one request in one launch, no device allocation (see include/fpt.h)."""
     _check(load().fpt_run_noalloc(ctypes.byref(p), n_traj, seed, d_steps, d_sums, d_hist, stream))
+
+
+def engine_occupancy(traj_per_thread: int, threads_per_block: int) -> int:
+    """CTAs of the resident kernel per SM for a launch shape (0: the shape cannot launch)."""
+    n = ctypes.c_int32(0)
+    _check(load().fpt_engine_occupancy(traj_per_thread, threads_per_block, ctypes.byref(n)))
+    return n.value
 
 
 def version() -> str:

@@ -1,14 +1,13 @@
 """Autotuner for the persistent engine's launch shape.
 
-Searches trajectories per thread, threads per block and resident blocks per SM on a short
-run of a given workload and returns the configuration with the highest useful trajectory-steps
+Searches trajectories per thread, threads per block and resident blocks per SM -- only shapes
+the kernel can launch, from fpt_engine_occupancy -- on a short run of a given workload and returns the configuration with the highest useful trajectory-steps
 per second of resident-kernel time (CUDA events inside the engine).  The step chunk is chosen
 afterwards: the shortest chunk whose per-iteration host overhead stays below `overhead` of the
 iteration time.
 """
 from __future__ import annotations
 
-import itertools
 import json
 import os
 import time
@@ -38,19 +37,25 @@ def _measure(requests, device, cfg, iters, chunk):
             "kernel_ms_per_iter": kms / iters, "wall_ms_per_iter": 1e3 * wall / iters}
 
 
+def launch_shapes(traj_per_thread=(1, 2), threads=(128, 256, 384, 512, 640)) -> list:
+    """Every (trajectories per thread, threads per block, CTAs per SM) the resident kernel can
+    launch on the current device, from the occupancy query of the C ABI."""
+    shapes = []
+    for T in traj_per_thread:
+        for tpb in threads:
+            for bps in range(1, _lib.engine_occupancy(T, tpb) + 1):
+                shapes.append({"traj_per_thread": T, "threads_per_block": tpb, "blocks_per_sm": bps})
+    return shapes
+
+
 def tune(requests, device: int = 0, iters: int = 3, chunk: int = 8192,
-         grid=None, overhead: float = 0.02, save: bool = True) -> dict:
-    """requests: list of (params dict, n_traj, seed).  Returns the best configuration."""
-    grid = grid or {"traj_per_thread": (1, 2), "threads_per_block": (128, 256, 512, 640),
-                    "blocks_per_sm": (0,)}
-    keys = sorted(grid)
+         shapes=None, overhead: float = 0.02, save: bool = True) -> dict:
+    """requests: list of (params dict, n_traj, seed).  Returns the best configuration.
+    shapes: list of engine options to try (default: every launchable shape, launch_shapes())."""
+    shapes = shapes if shapes is not None else launch_shapes()
     trials = []
-    for vals in itertools.product(*(grid[k] for k in keys)):
-        cfg = dict(zip(keys, vals))
-        try:
-            trials.append(_measure(requests, device, cfg, iters, chunk))
-        except _lib.FptError as e:
-            trials.append({"cfg": cfg, "error": str(e), "steps_per_s_kernel": 0.0})
+    for cfg in shapes:
+        trials.append(_measure(requests, device, dict(cfg), iters, chunk))
     best = max(trials, key=lambda r: r["steps_per_s_kernel"])
     # chunk: smallest power of two whose wall time per iteration is within `overhead` of the
     # kernel time (iteration cost = launch + scan + status copy + host processing)

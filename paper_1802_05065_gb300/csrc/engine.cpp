@@ -10,7 +10,16 @@
 //   5. the per-slot status and counters come back to pinned host memory.
 // Steps 2-5 are one CUDA graph.  Slots are reused only after no lane holds a trajectory of the
 // old request (its in-flight count has reached zero).
+//
+// Iterations are pipelined one deep: iteration i+1 is enqueued before the host waits for
+// iteration i and processes its status, so the GPU never idles while the host does admission,
+// list building and status processing.  Two sets of pinned buffers (lists uploaded, status
+// downloaded) and two graphs alternate.  Decisions taken on the host (admission, fair-share caps,
+// preemption) therefore see the status of two launches back; completion and the stop rule are
+// taken on the device by the scan kernel, so results do not depend on the lag.  fpt_step,
+// checkpoints and destruction drain the pipeline.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -60,6 +69,10 @@ struct Request {
     Clock::time_point t_submit;
     bool suspending = false;          // checkpoint requested: no new work, lanes park
     bool quiesced = false;            // no lane holds a trajectory; all suspended ones committed
+    // Iterations whose status may describe this request: from the first one enqueued after its
+    // admission (earlier ones show the slot's previous occupant), and for the quiesced test
+    // from the first one built with the suspension in force.
+    uint64_t admit_seq = 0, suspend_seq = UINT64_MAX;
     std::vector<uint8_t> restore;     // checkpoint payload to load at admission
 };
 
@@ -91,6 +104,20 @@ size_t request_bytes(const fpt_params &p, uint64_t n_traj, uint32_t B, unsigned 
 
 }  // namespace
 
+// Host side of one in-flight iteration: the lists it uploads, the status it downloads, its
+// events and its graph.  Two alternate.
+struct IterIO {
+    int *caps = nullptr, *act = nullptr, *act_count = nullptr;
+    int *preempt = nullptr, *flags = nullptr;   // flags: vacate[kNumKinds], strict, claim_warps
+    SlotCtl *ctl = nullptr;                     // status download target
+    unsigned long long *counters = nullptr;     // counters download target
+    cudaEvent_t k0 = nullptr, k1 = nullptr;     // around the resident kernel
+    cudaEvent_t done = nullptr;                 // after the downloads
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t seq = 0;                           // number of the iteration that used these buffers
+};
+
 struct fpt_engine {
     fpt_engine_config cfg{};
     int device = 0;
@@ -108,21 +135,20 @@ struct fpt_engine {
     unsigned *d_warp_cursor = nullptr;
     unsigned long long *d_counters = nullptr;
     EngineDev dev{};
-    // pinned host
+    // pinned host: admission staging, the last processed status and counters (stable copies read
+    // by fpt_poll, admission and list building), and the two alternating iteration buffers
     SlotDev *h_slots = nullptr;
     SlotCtl *h_ctl = nullptr, *h_ctl_init = nullptr;
-    int *h_caps = nullptr, *h_act = nullptr, *h_act_count = nullptr;
-    int *h_preempt = nullptr, *h_flags = nullptr;   // flags: vacate[kNumKinds], strict, claim_warps
-    uint64_t preempted = 0;
     unsigned long long *h_counters = nullptr;
-    int *h_state = nullptr;
-    // resident-kernel timing (events around the chunk kernel, recorded inside the graph)
-    cudaEvent_t ev_k0 = nullptr, ev_k1 = nullptr;
-    double kernel_ms = 0.0;
+    uint64_t preempted = 0;
+    IterIO iters[2];
+    int next_io = 0;              // buffers of the next iteration to enqueue
+    uint64_t enq_seq = 0;         // number of the next iteration to enqueue
+    uint64_t status_seq = UINT64_MAX;   // number of the iteration h_ctl comes from (none yet)
+    int flight[2] = {0, 0};       // enqueued, unprocessed iterations (buffer index), oldest first
+    std::atomic<int> n_flight{0};   // changed by the driving thread, read by the service loop
+    double kernel_ms = 0.0;       // summed resident-kernel time (events inside each iteration)
     bool capturing = false;
-    // graph
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
     // bookkeeping
     std::mutex mu, drive_mu;
     std::condition_variable cv_work, cv_done;
@@ -280,6 +306,7 @@ fpt_status admit(fpt_engine *e) {
         e->slot_req[s] = R.id;
         R.slot = s;
         R.phase = kRunning;
+        R.admit_seq = e->enq_seq;   // the coming launch is the first to see it
         it = e->pending.erase(it);
     }
     return FPT_OK;
@@ -291,28 +318,34 @@ fpt_status admit(fpt_engine *e) {
 // anyone is starved: caps are strict, requests above their share suspend the excess lanes at
 // the end of the launch, and if a starved request's kind (model x integrator) differs, whole
 // warps of other kinds vacate so they can switch.
-void build_lists(fpt_engine *e) {
+// Whether the last processed status describes request R (and not its slot's previous occupant).
+bool fresh(const fpt_engine *e, const Request &R) {
+    return e->status_seq != UINT64_MAX && e->status_seq >= R.admit_seq;
+}
+
+void build_lists(fpt_engine *e, IterIO &B) {
     int cnt[kNumKinds] = {};
     int active = 0;
     for (int s = 0; s < e->maxr; ++s) {
-        e->h_preempt[s] = 0;
+        B.preempt[s] = 0;
         if (!e->slot_req[s]) continue;
         Request &R = *e->reqs[e->slot_req[s]];
         if (R.phase != kRunning) continue;
         if (R.suspending) {                 // checkpoint: no new work, every lane suspends
-            e->h_preempt[s] = 1 << 30;
+            B.preempt[s] = 1 << 30;
+            if (R.suspend_seq == UINT64_MAX) R.suspend_seq = e->enq_seq;
             continue;
         }
-        e->h_act[R.dec.kind * e->maxr + cnt[R.dec.kind]++] = s;
+        B.act[R.dec.kind * e->maxr + cnt[R.dec.kind]++] = s;
         ++active;
     }
-    for (int k = 0; k < kNumKinds; ++k) e->h_act_count[k] = cnt[k];
+    for (int k = 0; k < kNumKinds; ++k) B.act_count[k] = cnt[k];
     const int share = active ? static_cast<int>((e->lanes + active - 1) / active) : 0;
     const int cap = active ? share + 32 : 0;
-    for (int s = 0; s < e->maxr; ++s) e->h_caps[s] = cap;
-    for (int k = 0; k <= kNumKinds; ++k) e->h_flags[k] = 0;
+    for (int s = 0; s < e->maxr; ++s) B.caps[s] = cap;
+    for (int k = 0; k <= kNumKinds; ++k) B.flags[k] = 0;
     for (int s = 0; s < e->maxr; ++s)
-        if (e->h_preempt[s]) e->h_flags[kNumKinds] = 1;   // keep a suspending request's lanes from refilling
+        if (B.preempt[s]) B.flags[kNumKinds] = 1;   // keep a suspending request's lanes from refilling
     // With fewer trajectories in flight and queued than lanes, only the first warps of every CTA
     // claim new work, so the busy warps spread over all SMs instead of filling a few of them.
     {
@@ -322,7 +355,7 @@ void build_lists(fpt_engine *e) {
             const Request &R = *e->reqs[e->slot_req[s]];
             if (R.phase != kRunning || R.suspending) continue;
             const SlotCtl &C = e->h_ctl[s];
-            if (C.state == kSlotActive) {
+            if (fresh(e, R) && C.state == kSlotActive) {
                 const uint64_t head = std::min<uint64_t>(C.head, R.n_traj);
                 work += static_cast<int64_t>(R.n_traj - head) + std::max(C.inflight, 0) +
                         std::max(C.park_avail, 0);
@@ -332,7 +365,7 @@ void build_lists(fpt_engine *e) {
         }
         const int64_t per_warp = 32ll * e->T * e->grid;
         const int64_t warps = (work + per_warp - 1) / per_warp;
-        e->h_flags[kNumKinds + 1] =
+        B.flags[kNumKinds + 1] =
             static_cast<int>(std::min<int64_t>(std::max<int64_t>(warps, 1), e->block / 32));
     }
     if (active < 2) return;
@@ -343,7 +376,7 @@ void build_lists(fpt_engine *e) {
         Request &R = *e->reqs[e->slot_req[s]];
         if (R.phase != kRunning || R.suspending) continue;
         const SlotCtl &C = e->h_ctl[s];
-        if (C.state != kSlotActive) continue;     // not yet launched or finishing
+        if (!fresh(e, R) || C.state != kSlotActive) continue;     // not yet launched or finishing
         const int64_t unclaimed = C.head < R.n_traj ? static_cast<int64_t>(R.n_traj - C.head) : 0;
         const int64_t remaining = unclaimed + std::max(C.park_avail, 0);
         const int64_t want = std::min<int64_t>(share, C.inflight + remaining);
@@ -353,45 +386,45 @@ void build_lists(fpt_engine *e) {
     int64_t total_deficit = 0;
     for (int k = 0; k < kNumKinds; ++k) total_deficit += deficit[k];
     if (total_deficit == 0) return;
-    e->h_flags[kNumKinds] = 1;   // strict caps
+    B.flags[kNumKinds] = 1;   // strict caps
     for (int s = 0; s < e->maxr; ++s) {
         if (!e->slot_req[s]) continue;
         Request &R = *e->reqs[e->slot_req[s]];
         if (R.phase != kRunning || R.suspending) continue;
         const SlotCtl &C = e->h_ctl[s];
-        if (C.state != kSlotActive || C.inflight <= share) continue;
+        if (!fresh(e, R) || C.state != kSlotActive || C.inflight <= share) continue;
         const int room = static_cast<int>(R.park_cap) - std::max(C.park_used, 0);
-        e->h_preempt[s] = std::max(0, std::min(C.inflight - share, room));
-        e->preempted += static_cast<uint64_t>(e->h_preempt[s]);
+        B.preempt[s] = std::max(0, std::min(C.inflight - share, room));
+        e->preempted += static_cast<uint64_t>(B.preempt[s]);
     }
     const int64_t lanes_per_warp = 32ll * e->T;
     for (int m = 0; m < kNumKinds; ++m) {
         const int64_t others = total_deficit - deficit[m];
         if (others > 0 && over[m])
-            e->h_flags[m] = static_cast<int>((others + lanes_per_warp - 1) / lanes_per_warp);
+            B.flags[m] = static_cast<int>((others + lanes_per_warp - 1) / lanes_per_warp);
     }
 }
 
-fpt_status enqueue_iteration(fpt_engine *e) {
-    if (e->exec) {
-        CK(cudaGraphLaunch(e->exec, e->stream));
+fpt_status enqueue_iteration(fpt_engine *e, IterIO &B) {
+    if (B.exec) {
+        CK(cudaGraphLaunch(B.exec, e->stream));
         return FPT_OK;
     }
-    CK(cudaMemcpyAsync(e->d_caps, e->h_caps, e->maxr * sizeof(int), cudaMemcpyHostToDevice, e->stream));
-    CK(cudaMemcpyAsync(e->d_preempt, e->h_preempt, e->maxr * sizeof(int), cudaMemcpyHostToDevice, e->stream));
-    CK(cudaMemcpyAsync(e->d_vacate, e->h_flags, (kNumKinds + 2) * sizeof(int), cudaMemcpyHostToDevice,
+    CK(cudaMemcpyAsync(e->d_caps, B.caps, e->maxr * sizeof(int), cudaMemcpyHostToDevice, e->stream));
+    CK(cudaMemcpyAsync(e->d_preempt, B.preempt, e->maxr * sizeof(int), cudaMemcpyHostToDevice, e->stream));
+    CK(cudaMemcpyAsync(e->d_vacate, B.flags, (kNumKinds + 2) * sizeof(int), cudaMemcpyHostToDevice,
                        e->stream));
-    CK(cudaMemcpyAsync(e->d_act, e->h_act, kNumKinds * e->maxr * sizeof(int), cudaMemcpyHostToDevice,
+    CK(cudaMemcpyAsync(e->d_act, B.act, kNumKinds * e->maxr * sizeof(int), cudaMemcpyHostToDevice,
                        e->stream));
-    CK(cudaMemcpyAsync(e->d_act_count, e->h_act_count, kNumKinds * sizeof(int), cudaMemcpyHostToDevice,
+    CK(cudaMemcpyAsync(e->d_act_count, B.act_count, kNumKinds * sizeof(int), cudaMemcpyHostToDevice,
                        e->stream));
     const unsigned evflags = e->capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
-    CK(cudaEventRecordWithFlags(e->ev_k0, e->stream, evflags));
+    CK(cudaEventRecordWithFlags(B.k0, e->stream, evflags));
     CK(launch_engine_chunk(e->dev, e->T, e->grid, e->block, e->stream));
-    CK(cudaEventRecordWithFlags(e->ev_k1, e->stream, evflags));
+    CK(cudaEventRecordWithFlags(B.k1, e->stream, evflags));
     CK(launch_engine_scan(e->dev, e->stream));
-    CK(cudaMemcpyAsync(e->h_ctl, e->d_ctl, e->maxr * sizeof(SlotCtl), cudaMemcpyDeviceToHost, e->stream));
-    CK(cudaMemcpyAsync(e->h_counters, e->d_counters, kCntCount * sizeof(unsigned long long),
+    CK(cudaMemcpyAsync(B.ctl, e->d_ctl, e->maxr * sizeof(SlotCtl), cudaMemcpyDeviceToHost, e->stream));
+    CK(cudaMemcpyAsync(B.counters, e->d_counters, kCntCount * sizeof(unsigned long long),
                        cudaMemcpyDeviceToHost, e->stream));
     return FPT_OK;
 }
@@ -418,17 +451,19 @@ void finalize(fpt_engine *e, Request &R, const SlotCtl &C) {
     (void)e;
 }
 
-// Read the status of the last iteration (mu held).
+// Read the status of the last processed iteration (mu held).
 void process_status(fpt_engine *e) {
     for (int s = 0; s < e->maxr; ++s) {
         if (!e->slot_req[s]) continue;
         Request &R = *e->reqs[e->slot_req[s]];
+        if (!fresh(e, R)) continue;   // launched before R was admitted: the previous occupant
         const SlotCtl &C = e->h_ctl[s];
         if (R.phase == kRunning && C.state == kSlotFinished) {
             finalize(e, R, C);
             R.phase = kFinished;
         }
-        if (R.phase == kRunning && R.suspending && C.inflight == 0 && C.park_commit == C.park_tail)
+        if (R.phase == kRunning && R.suspending && R.suspend_seq != UINT64_MAX &&
+            e->status_seq >= R.suspend_seq && C.inflight == 0 && C.park_commit == C.park_tail)
             R.quiesced = true;
         if ((R.phase == kFinished || R.phase == kCancelled) && C.state != kSlotActive &&
             C.inflight == 0) {
@@ -442,26 +477,61 @@ void process_status(fpt_engine *e) {
     }
 }
 
-fpt_status iteration(fpt_engine *e) {
-    if (e->broken) return fail(e, FPT_ECUDA, "engine is in an error state: " + e->error);
-    {
-        std::lock_guard<std::mutex> lk(e->mu);
-        fpt_status st = admit(e);
-        if (st != FPT_OK) return st;
-        build_lists(e);
-    }
-    fpt_status st = enqueue_iteration(e);
-    if (st != FPT_OK) return st;
-    CK(cudaStreamSynchronize(e->stream));
+// Wait for the oldest enqueued iteration and take its status: stable copies for fpt_poll,
+// admission and list building, finished requests, freed slots, counters and kernel time.
+fpt_status complete_oldest(fpt_engine *e) {
+    IterIO &B = e->iters[e->flight[0]];
+    CK(cudaEventSynchronize(B.done));
     float ms = 0.0f;
-    CK(cudaEventElapsedTime(&ms, e->ev_k0, e->ev_k1));
+    CK(cudaEventElapsedTime(&ms, B.k0, B.k1));
     {
         std::lock_guard<std::mutex> lk(e->mu);
+        std::memcpy(e->h_ctl, B.ctl, e->maxr * sizeof(SlotCtl));
+        std::memcpy(e->h_counters, B.counters, kCntCount * sizeof(unsigned long long));
+        e->status_seq = B.seq;
         process_status(e);
         ++e->iterations;
         e->kernel_ms += ms;
     }
+    e->flight[0] = e->flight[1];
+    --e->n_flight;
     e->cv_done.notify_all();
+    return FPT_OK;
+}
+
+// One engine iteration: admission and lists from the last processed status, enqueue, then
+// process the previous iteration's status while this one runs (at most one iteration stays
+// enqueued and unprocessed when this returns).
+fpt_status iteration(fpt_engine *e) {
+    if (e->broken) return fail(e, FPT_ECUDA, "engine is in an error state: " + e->error);
+    if (e->n_flight == 2) {
+        const fpt_status st = complete_oldest(e);
+        if (st != FPT_OK) return st;
+    }
+    IterIO &B = e->iters[e->next_io];
+    {
+        std::lock_guard<std::mutex> lk(e->mu);
+        fpt_status st = admit(e);
+        if (st != FPT_OK) return st;
+        build_lists(e, B);
+    }
+    B.seq = e->enq_seq++;
+    fpt_status st = enqueue_iteration(e, B);
+    if (st != FPT_OK) return st;
+    CK(cudaEventRecord(B.done, e->stream));
+    e->flight[e->n_flight.load()] = e->next_io;
+    ++e->n_flight;
+    e->next_io ^= 1;
+    if (e->n_flight == 2) return complete_oldest(e);
+    return FPT_OK;
+}
+
+// Process every enqueued iteration (the device has finished all of them on return).
+fpt_status drain(fpt_engine *e) {
+    while (e->n_flight > 0) {
+        const fpt_status st = complete_oldest(e);
+        if (st != FPT_OK) return st;
+    }
     return FPT_OK;
 }
 
@@ -474,34 +544,36 @@ bool has_work(fpt_engine *e) {
 
 void service_loop(fpt_engine *e) {
     for (;;) {
+        bool work;
         {
             std::unique_lock<std::mutex> lk(e->mu);
-            e->cv_work.wait(lk, [&] { return e->stop || has_work(e); });
+            e->cv_work.wait(lk, [&] { return e->stop || has_work(e) || e->n_flight > 0; });
             if (e->stop) return;
+            work = has_work(e);
         }
         std::lock_guard<std::mutex> dk(e->drive_mu);
-        if (iteration(e) != FPT_OK) {
+        if ((work ? iteration(e) : drain(e)) != FPT_OK) {
             e->cv_done.notify_all();
             return;
         }
     }
 }
 
-fpt_status capture_graph(fpt_engine *e) {
+fpt_status capture_graph(fpt_engine *e, IterIO &B) {
     CK(cudaStreamBeginCapture(e->stream, cudaStreamCaptureModeThreadLocal));
     fpt_status st = FPT_OK;
     {
-        e->exec = nullptr;
+        B.exec = nullptr;
         e->capturing = true;
-        st = enqueue_iteration(e);
+        st = enqueue_iteration(e, B);
         e->capturing = false;
     }
     cudaGraph_t g = nullptr;
     const cudaError_t ce = cudaStreamEndCapture(e->stream, &g);
     if (st != FPT_OK) return st;
     CK(ce);
-    e->graph = g;
-    CK(cudaGraphInstantiate(&e->exec, e->graph, 0));
+    B.graph = g;
+    CK(cudaGraphInstantiate(&B.exec, B.graph, 0));
     return FPT_OK;
 }
 
@@ -516,10 +588,23 @@ void destroy_all(fpt_engine *e) {
     }
     cudaSetDevice(e->device);
     if (e->stream) cudaStreamSynchronize(e->stream);
+    e->n_flight = 0;
     for (auto &kv : e->reqs) free_request_buffers(*kv.second, e);
     e->reqs.clear();
-    if (e->exec) cudaGraphExecDestroy(e->exec);
-    if (e->graph) cudaGraphDestroy(e->graph);
+    for (IterIO &B : e->iters) {
+        if (B.exec) cudaGraphExecDestroy(B.exec);
+        if (B.graph) cudaGraphDestroy(B.graph);
+        cudaFreeHost(B.caps);
+        cudaFreeHost(B.act);
+        cudaFreeHost(B.act_count);
+        cudaFreeHost(B.preempt);
+        cudaFreeHost(B.flags);
+        cudaFreeHost(B.ctl);
+        cudaFreeHost(B.counters);
+        if (B.k0) cudaEventDestroy(B.k0);
+        if (B.k1) cudaEventDestroy(B.k1);
+        if (B.done) cudaEventDestroy(B.done);
+    }
     cudaFree(e->d_slots);
     cudaFree(e->d_ctl);
     cudaFree(e->d_caps);
@@ -534,14 +619,7 @@ void destroy_all(fpt_engine *e) {
     cudaFreeHost(e->h_slots);
     cudaFreeHost(e->h_ctl);
     cudaFreeHost(e->h_ctl_init);
-    cudaFreeHost(e->h_caps);
-    cudaFreeHost(e->h_act);
-    cudaFreeHost(e->h_act_count);
-    cudaFreeHost(e->h_preempt);
-    cudaFreeHost(e->h_flags);
     cudaFreeHost(e->h_counters);
-    if (e->ev_k0) cudaEventDestroy(e->ev_k0);
-    if (e->ev_k1) cudaEventDestroy(e->ev_k1);
     if (e->io) cudaStreamDestroy(e->io);
     if (e->own_stream && e->stream) cudaStreamDestroy(e->stream);
 }
@@ -586,8 +664,6 @@ fpt_status create_impl(const fpt_engine_config *cfg_in, fpt_engine *e) {
         e->own_stream = true;
     }
     CK(cudaStreamCreateWithFlags(&e->io, cudaStreamNonBlocking));
-    CK(cudaEventCreate(&e->ev_k0));
-    CK(cudaEventCreate(&e->ev_k1));
     const int R = e->maxr;
     CK(cudaMalloc(&e->d_slots, R * sizeof(SlotDev)));
     CK(cudaMalloc(&e->d_ctl, R * sizeof(SlotCtl)));
@@ -630,19 +706,28 @@ fpt_status create_impl(const fpt_engine_config *cfg_in, fpt_engine *e) {
     CK(cudaMallocHost(&e->h_slots, R * sizeof(SlotDev)));
     CK(cudaMallocHost(&e->h_ctl, R * sizeof(SlotCtl)));
     CK(cudaMallocHost(&e->h_ctl_init, R * sizeof(SlotCtl)));
-    CK(cudaMallocHost(&e->h_caps, R * sizeof(int)));
-    CK(cudaMallocHost(&e->h_act, kNumKinds * R * sizeof(int)));
-    CK(cudaMallocHost(&e->h_act_count, kNumKinds * sizeof(int)));
-    CK(cudaMallocHost(&e->h_preempt, R * sizeof(int)));
-    CK(cudaMallocHost(&e->h_flags, (kNumKinds + 2) * sizeof(int)));
-    std::memset(e->h_preempt, 0, R * sizeof(int));
-    std::memset(e->h_flags, 0, (kNumKinds + 2) * sizeof(int));
     CK(cudaMallocHost(&e->h_counters, kCntCount * sizeof(unsigned long long)));
     std::memset(e->h_ctl, 0, R * sizeof(SlotCtl));
-    std::memset(e->h_caps, 0, R * sizeof(int));
-    std::memset(e->h_act, 0, kNumKinds * R * sizeof(int));
-    std::memset(e->h_act_count, 0, kNumKinds * sizeof(int));
     std::memset(e->h_counters, 0, kCntCount * sizeof(unsigned long long));
+    for (IterIO &B : e->iters) {
+        CK(cudaMallocHost(&B.caps, R * sizeof(int)));
+        CK(cudaMallocHost(&B.act, kNumKinds * R * sizeof(int)));
+        CK(cudaMallocHost(&B.act_count, kNumKinds * sizeof(int)));
+        CK(cudaMallocHost(&B.preempt, R * sizeof(int)));
+        CK(cudaMallocHost(&B.flags, (kNumKinds + 2) * sizeof(int)));
+        CK(cudaMallocHost(&B.ctl, R * sizeof(SlotCtl)));
+        CK(cudaMallocHost(&B.counters, kCntCount * sizeof(unsigned long long)));
+        std::memset(B.caps, 0, R * sizeof(int));
+        std::memset(B.act, 0, kNumKinds * R * sizeof(int));
+        std::memset(B.act_count, 0, kNumKinds * sizeof(int));
+        std::memset(B.preempt, 0, R * sizeof(int));
+        std::memset(B.flags, 0, (kNumKinds + 2) * sizeof(int));
+        std::memset(B.ctl, 0, R * sizeof(SlotCtl));
+        std::memset(B.counters, 0, kCntCount * sizeof(unsigned long long));
+        CK(cudaEventCreate(&B.k0));
+        CK(cudaEventCreate(&B.k1));
+        CK(cudaEventCreateWithFlags(&B.done, cudaEventDisableTiming));
+    }
     e->slot_req.assign(R, 0);
     EngineDev &d = e->dev;
     d.slots = e->d_slots;
@@ -660,10 +745,11 @@ fpt_status create_impl(const fpt_engine_config *cfg_in, fpt_engine *e) {
     d.chunk_blocks = e->chunk_blocks;
     d.max_requests = R;
     CK(cudaStreamSynchronize(e->stream));
-    if (cfg.use_graph) {
-        fpt_status st = capture_graph(e);
-        if (st != FPT_OK) return st;
-    }
+    if (cfg.use_graph)
+        for (IterIO &B : e->iters) {
+            fpt_status st = capture_graph(e, B);
+            if (st != FPT_OK) return st;
+        }
     if (cfg.service_thread) e->service = std::thread(service_loop, e);
     return FPT_OK;
 }
@@ -741,7 +827,7 @@ extern "C" fpt_status fpt_step(fpt_engine *e, int n_iterations) {
         const fpt_status st = iteration(e);
         if (st != FPT_OK) return st;
     }
-    return FPT_OK;
+    return drain(e);
 }
 
 extern "C" fpt_status fpt_poll(fpt_engine *e, uint64_t req_id, fpt_result *out) {
@@ -755,7 +841,7 @@ extern "C" fpt_status fpt_poll(fpt_engine *e, uint64_t req_id, fpt_result *out) 
     }
     std::memset(out, 0, sizeof(*out));
     out->state = FPT_PENDING;
-    if (R->slot >= 0) {
+    if (R->slot >= 0 && fresh(e, *R)) {
         const SlotCtl &C = e->h_ctl[R->slot];
         out->n_used = C.n_done;
         out->n_escaped = C.n_esc;
@@ -919,10 +1005,14 @@ extern "C" fpt_status fpt_checkpoint(fpt_engine *e, uint64_t req_id, void *buf, 
         if (st != FPT_OK) return st;
     }
     std::lock_guard<std::mutex> dk(e->drive_mu);   // no launch may run while we read
+    CK(cudaSetDevice(e->device));
+    {
+        const fpt_status ds = drain(e);
+        if (ds != FPT_OK) return ds;
+    }
     std::lock_guard<std::mutex> lk(e->mu);
     Request *R = find(e, req_id);
     if (!R) return fail(e, FPT_ENOTFOUND, "request vanished");
-    CK(cudaSetDevice(e->device));
     uint8_t *q = static_cast<uint8_t *>(buf);
     CkptHeader H{};
     H.magic = kCkptMagic;
@@ -1062,6 +1152,22 @@ extern "C" fpt_status fpt_get_counters(fpt_engine *e, fpt_engine_counters *out) 
     for (int s = 0; s < e->maxr; ++s)
         if (e->slot_req[s]) ++out->resident_requests;
     out->pending_requests = static_cast<uint32_t>(e->pending.size());
+    return FPT_OK;
+}
+
+extern "C" fpt_status fpt_engine_occupancy(int32_t traj_per_thread, int32_t threads_per_block,
+                                           int32_t *blocks_per_sm) {
+    if (!blocks_per_sm) return fail(nullptr, FPT_EINVAL, "blocks_per_sm is NULL");
+    *blocks_per_sm = 0;
+    if (traj_per_thread != 1 && traj_per_thread != 2)
+        return fail(nullptr, FPT_EINVAL, "traj_per_thread must be 1 or 2");
+    const int max_block = traj_per_thread == 1 ? 640 : 256;
+    if (threads_per_block < 32 || threads_per_block % 32 || threads_per_block > max_block)
+        return FPT_OK;   // the kernel cannot launch with this shape: 0 CTAs per SM
+    int bps = 0;
+    const cudaError_t ce = engine_chunk_occupancy(traj_per_thread, threads_per_block, &bps);
+    if (ce != cudaSuccess) return fail(nullptr, FPT_ECUDA, std::string("occupancy: ") + cudaGetErrorString(ce));
+    *blocks_per_sm = bps;
     return FPT_OK;
 }
 
