@@ -607,9 +607,14 @@ def run_ours(args):
         ramp = [(d, n_traj, d["seed"]) for d in workloads.ramp_sweep(n_traj=n_traj)]
         ub = [(d, d["n_traj"], d["seed"]) for d in workloads.uneven_batch()]
         li = workloads.li07_switching()
+        short = workloads.scaled(pts[11], dt=0.02, max_steps=10**6)
         mix = {"ramp_sweep": _leg(ramp, 5, 65536),
                "uneven_batch": _leg(ub, 10, 16384),
-               "li07_device": _leg([(li, li["n_traj"], li["seed"])], 5, 65536)}
+               "li07_device": _leg([(li, li["n_traj"], li["seed"])], 5, 65536),
+               "short_trajectories": _leg([(short, 2**24, short["seed"])], 10, 4096)}
+        mix["short_trajectories"]["workload"] = (
+            "overdamped gamma=0.9 D=0.2 at dt=0.02 (mean ~950 steps per trajectory), 2^24 "
+            "trajectories: escapes/s with warp-aggregated result emission")
         mix["li07_device"]["workload"] = ("the Fig. 10b junction (Li07 parameters), 30 000 "
                                           "trajectories at the paper's ramp, first iterations")
         mix["ramp_sweep"]["workload"] = "ramp sweep nu {1e-5..1e-8}, 4 x 2^20 trajectories"

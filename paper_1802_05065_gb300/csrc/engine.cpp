@@ -86,7 +86,7 @@ struct CkptHeader {
     uint64_t n_park, has_per_traj;
 };
 constexpr uint64_t kCkptMagic = 0x5450464B43505446ull;   // "FTPCKFPT"
-constexpr uint64_t kCkptVersion = 2;   // 2: Philox block counts are multiples of kBlockPhilox
+constexpr uint64_t kCkptVersion = 3;   // 3: id-block sums kept as 32-bit limbs
 
 // Ring of suspended trajectories: never more than the lanes can hold twice over.
 uint32_t park_capacity(uint64_t n_traj, unsigned lanes) {
@@ -635,7 +635,7 @@ fpt_status create_impl(const fpt_engine_config *cfg_in, fpt_engine *e) {
     if (cfg.device < 0 || cfg.device >= ndev) return fail(e, FPT_EINVAL, "bad device ordinal");
     CK(cudaSetDevice(cfg.device));
     e->maxr = cfg.max_requests > 0 ? cfg.max_requests : 256;
-    if (e->maxr > 1024) return fail(e, FPT_EINVAL, "max_requests must be <= 1024");
+    if (e->maxr > kMaxRequests) return fail(e, FPT_EINVAL, "max_requests must be <= 1024");
     e->T = cfg.traj_per_thread > 0 ? cfg.traj_per_thread : 1;
     if (e->T != 1 && e->T != 2) return fail(e, FPT_EINVAL, "traj_per_thread must be 1 or 2");
     const int max_block = e->T == 1 ? 640 : 256;

@@ -22,6 +22,9 @@ enum : int { kSlotFree = 0, kSlotActive = 1, kSlotFinished = 2, kSlotCancelled =
 // x Euler-Maruyama / Heun x constant / ramped bias).  A warp runs one kind at a time.
 constexpr int kNumKinds = 8;
 
+// Resident request slots an engine may have (the kernel keeps a per-slot view in shared memory).
+constexpr int kMaxRequests = 1024;
+
 // Philox blocks (of 4 steps) between re-bases of a trajectory's single-precision bias: gamma_k is
 // formed as gs + nu dt (s + 1) with gs = gb + nu dt Jf and gb = gamma0 + nu dt 4 c_base in FP64,
 // c_base the trajectory's own block count rounded down to a multiple of kRebaseBlocks, so the
@@ -35,11 +38,15 @@ struct ParkEntry {
     unsigned c_lo, c_hi, gid_lo, gid_hi, pad;
 };
 
-// Exact accumulators of one block of stop_block consecutive trajectory ids.
+// Exact accumulators of one block of stop_block (<= 2^32) consecutive trajectory ids.  The sums
+// of k (< 2^48) and k^2 (< 2^96) are kept as sums of their 32-bit limbs, each in 64 bits, so a
+// trajectory adds to them with plain atomic additions whose result nobody waits for (no carry
+// to propagate); the scan kernel combines the limbs into 128-bit sums:
+//   sum k = s1[0] + 2^32 s1[1],   sum k^2 = s2[0] + 2^32 s2[1] + 2^64 s2[2].
 struct IdBlockAcc {
     unsigned int done, escaped, under, over;
-    unsigned long long s1_lo, s1_hi;   // sum of escape steps (128-bit)
-    unsigned long long s2_lo, s2_hi;   // sum of squared escape steps (128-bit)
+    unsigned long long s1[2];   // limbs of the sum of escape steps
+    unsigned long long s2[3];   // limbs of the sum of squared escape steps
 };
 
 struct SlotDev {

@@ -136,32 +136,99 @@ __device__ __forceinline__ void atomic_add128(unsigned long long *lo_p, unsigned
     if (ahi + carry) atomicAdd(hi_p, ahi + carry);
 }
 
-// Publish one finished trajectory into its id block: exact sums of k and k^2, histogram bin of
-// x = out_a + out_b k (IEEE double, separately rounded), optional per-trajectory step, then the
-// completion count that the scan kernel reads.
-__device__ __forceinline__ void emit(const SlotDev *S, unsigned long long gid, bool escaped, unsigned long long k) {
-    const unsigned long long idx = gid - S->traj_offset;
-    const unsigned ib = static_cast<unsigned>(idx / S->stop_block);
+// Histogram bin of x = out_a + out_b k (IEEE double, separately rounded): -1 below the range,
+// hist_bins above it.
+__device__ __forceinline__ int hist_bin(const SlotDev *S, unsigned long long k) {
+    const double kd = static_cast<double>(k);
+    const double x = S->output == FPT_OUT_TIME ? __dmul_rn(S->out_b, kd)
+                                               : __dadd_rn(S->out_a, __dmul_rn(S->out_b, kd));
+    if (x < S->hist_lo) return -1;
+    if (x >= S->hist_hi) return S->hist_bins;
+    const int bin = static_cast<int>(floor(__dmul_rn(__dsub_rn(x, S->hist_lo), S->hist_inv_w)));
+    return bin < S->hist_bins ? bin : S->hist_bins - 1;
+}
+
+// Per-CTA view of the requests during one launch (shared memory), set up at kernel start:
+//   ok[s]   bit 0: request s has ids left to claim, bit 1: it has suspended trajectories to
+//           resume (both as of the launch start; cleared when a warp finds them exhausted),
+//   held[s] lanes of this CTA that hold a trajectory of s (the CTA's share of the fair-share
+//           cap is checked against it, so claims need no global read).
+struct CtaView {
+    unsigned *ok;
+    int *held;
+};
+
+// Publish the trajectories finishing in this warp at this block end (warp-collective: every lane
+// calls it, `fin` says whether its trajectory finished).  Lanes are grouped by (request slot, id
+// block) with a match; each group's counts and the 32-bit limbs of k and k^2 are gathered by
+// shuffles, and its first lane adds them into the id block with atomic additions whose result
+// it does not wait for, and gives back the group's in-flight places.  Histogram counts are
+// grouped by (slot, id block, bin) the same way.  The scan kernel reads the id blocks only
+// after the launch, so the order of the additions is free.
+__device__ __forceinline__ void emit_warp(const EngineDev &E, const CtaView &V, bool fin, int slot,
+                                          unsigned long long gid, bool escaped, unsigned long long k) {
+    const int lane = threadIdx.x & 31;
+    const SlotDev *S = E.slots + (fin ? slot : 0);
+    unsigned long long idx = 0;
+    unsigned ib = 0;
+    int bin = -2;
+    if (fin) {
+        idx = gid - S->traj_offset;
+        ib = static_cast<unsigned>(idx / S->stop_block);
+        if (escaped) bin = hist_bin(S, k);
+        if (S->per_traj) S->per_traj[idx] = escaped ? static_cast<long long>(k) : -1ll;
+    }
+    // slot < 2^10, id block < 2^32, bin < 2^21: distinct keys for distinct groups
+    const unsigned long long gkey = fin ? (static_cast<unsigned long long>(slot) << 32) | ib : ~0ull;
+    const unsigned grp = __match_any_sync(kFull, gkey);
+    const unsigned long long bkey =
+        fin && bin >= 0 && bin < S->hist_bins
+            ? (static_cast<unsigned long long>(slot) << 53) | (static_cast<unsigned long long>(ib) << 21) |
+                  static_cast<unsigned long long>(bin)
+            : ~0ull;
+    const unsigned bgrp = __match_any_sync(kFull, bkey);
+    if (!fin) return;
     IdBlockAcc *A = S->acc + ib;
-    if (escaped) {
-        atomicAdd(&A->escaped, 1u);
-        atomic_add128(&A->s1_lo, &A->s1_hi, k, 0ull);
-        atomic_add128(&A->s2_lo, &A->s2_hi, k * k, __umul64hi(k, k));
-        const double kd = static_cast<double>(k);
-        const double x = S->output == FPT_OUT_TIME ? __dmul_rn(S->out_b, kd)
-                                                   : __dadd_rn(S->out_a, __dmul_rn(S->out_b, kd));
-        if (x < S->hist_lo) {
-            atomicAdd(&A->under, 1u);
-        } else if (x >= S->hist_hi) {
-            atomicAdd(&A->over, 1u);
-        } else {
-            int bin = static_cast<int>(floor(__dmul_rn(__dsub_rn(x, S->hist_lo), S->hist_inv_w)));
-            if (bin >= S->hist_bins) bin = S->hist_bins - 1;
-            atomicAdd(S->hist + static_cast<size_t>(ib) * S->hist_bins + bin, 1u);
+    if (bkey != ~0ull && lane == __ffs(bgrp) - 1)
+        atomicAdd(S->hist + static_cast<size_t>(ib) * S->hist_bins + bin, static_cast<unsigned>(__popc(bgrp)));
+    // limbs: k = k0 + 2^32 k1, k^2 = q0 + 2^32 q1 + 2^64 q2 (each < 2^32)
+    const unsigned long long kk_lo = escaped ? k * k : 0ull, kk_hi = escaped ? __umul64hi(k, k) : 0ull;
+    const unsigned long long ke = escaped ? k : 0ull;
+    unsigned long long l[5] = {ke & 0xFFFFFFFFull, ke >> 32, kk_lo & 0xFFFFFFFFull, kk_lo >> 32, kk_hi};
+    unsigned cnt = (escaped ? 1u : 0u) | (bin == -1 ? 2u : 0u) | (escaped && bin == S->hist_bins ? 4u : 0u);
+    unsigned n_e = cnt & 1u, n_u = (cnt >> 1) & 1u, n_o = cnt >> 2;
+    const int leader = __ffs(grp) - 1;
+    unsigned rest = grp & ~(1u << leader);
+    while (rest) {   // every lane of the group runs the same sequence of shuffles
+        const int src = __ffs(rest) - 1;
+        rest &= rest - 1u;
+        const unsigned c = __shfl_sync(grp, cnt, src);
+        unsigned long long m[5];
+#pragma unroll
+        for (int j = 0; j < 5; ++j) m[j] = __shfl_sync(grp, l[j], src);   // src's l is unchanged
+        if (lane == leader) {
+            n_e += c & 1u;
+            n_u += (c >> 1) & 1u;
+            n_o += c >> 2;
+#pragma unroll
+            for (int j = 0; j < 5; ++j) l[j] += m[j];
         }
     }
-    if (S->per_traj) S->per_traj[idx] = escaped ? static_cast<long long>(k) : -1ll;
-    atomicAdd(&A->done, 1u);
+    if (lane != leader) return;
+    if (n_e) {
+        atomicAdd(&A->escaped, n_e);
+        atomicAdd(&A->s1[0], l[0]);
+        if (l[1]) atomicAdd(&A->s1[1], l[1]);
+        atomicAdd(&A->s2[0], l[2]);
+        if (l[3]) atomicAdd(&A->s2[1], l[3]);
+        if (l[4]) atomicAdd(&A->s2[2], l[4]);
+    }
+    if (n_u) atomicAdd(&A->under, n_u);
+    if (n_o) atomicAdd(&A->over, n_o);
+    const int n = __popc(grp);
+    atomicAdd(&A->done, static_cast<unsigned>(n));
+    atomicSub(&E.ctl[slot].inflight, n);
+    atomicSub(&V.held[slot], n);
 }
 
 // Rare per-lane path: the phase reached hb = min(eb, pi), where eb = phi* - 2 pi w is the
@@ -190,47 +257,53 @@ __device__ __forceinline__ void wrap_down(Lane &L, const EngineDev &E) {
     L.hb = fminf(fmaf(-kTwoPiF, static_cast<float>(L.w - S->w0), S->eb0), kPiF);
 }
 
-// Finish lanes that escaped in the last block or reached the step budget.
+// Finish lanes that escaped in the last block or reached the step budget (warp-collective).
 template <int T>
-__device__ __forceinline__ void finish_lanes(Lane (&L)[T], const EngineDev &E, unsigned long long &useful,
-                             int &n_active, unsigned &n_esc, unsigned &n_cens) {
+__device__ __forceinline__ void finish_lanes(Lane (&L)[T], const EngineDev &E, const CtaView &V,
+                                             unsigned long long &useful, int &n_active, unsigned &n_esc,
+                                             unsigned &n_cens) {
 #pragma unroll
     for (int t = 0; t < T; ++t) {
+        bool fin = false, escaped = false;
+        unsigned long long k = 0;
         if (L[t].slot < 0) {
             L[t].budget = 0xFFFFFFFFu;
-            continue;
+        } else if (L[t].esc >= 0 || L[t].budget == 0) {
+            const SlotDev *S = E.slots + L[t].slot;
+            const unsigned long long c = lane_c(L[t]);
+            const unsigned long long max_steps = S->max_steps;
+            if (L[t].esc < 0 && c < S->nblocks) {   // re-base of the bias, not the end of the budget
+                set_progress(L[t], S);
+            } else {
+                fin = true;
+                if (L[t].esc >= 0) {
+                    k = 4ull * (c - kBlockPhilox) + static_cast<unsigned long long>(L[t].esc) + 1ull;
+                    escaped = k <= max_steps;
+                }
+                if (escaped) useful -= static_cast<unsigned long long>(kBlockSteps - 1 - L[t].esc);
+                else useful -= 4ull * c - max_steps;
+            }
         }
-        const bool esc = L[t].esc >= 0;
-        if (!esc && L[t].budget != 0) continue;
-        const SlotDev *S = E.slots + L[t].slot;
-        const unsigned long long c = lane_c(L[t]);
-        const unsigned long long max_steps = S->max_steps;
-        if (!esc && c < S->nblocks) {   // re-base of the bias, not the end of the budget
-            set_progress(L[t], S);
-            continue;
-        }
-        unsigned long long k = 0;
-        bool escaped = false;
-        if (esc) {
-            k = 4ull * (c - kBlockPhilox) + static_cast<unsigned long long>(L[t].esc) + 1ull;
-            escaped = k <= max_steps;
-        }
-        if (escaped) useful -= static_cast<unsigned long long>(kBlockSteps - 1 - L[t].esc);
-        else useful -= 4ull * c - max_steps;
         const unsigned long long gid = (static_cast<unsigned long long>(L[t].gid_hi) << 32) | L[t].gid_lo;
-        emit(S, gid, escaped, k);
-        if (escaped) ++n_esc;
-        else ++n_cens;
-        atomicSub(&E.ctl[L[t].slot].inflight, 1);
-        set_idle(L[t]);
-        --n_active;
+        emit_warp(E, V, fin, L[t].slot, gid, escaped, k);
+        if (fin) {
+            if (escaped) ++n_esc;
+            else ++n_cens;
+            set_idle(L[t]);
+            --n_active;
+        }
     }
 }
 
-// Warp-collective refill of idle lanes with trajectories of requests of kind `kind`.
+// Warp-collective refill of idle lanes with trajectories of requests of kind `kind`.  Lane 0
+// takes, per request in round-robin order, suspended trajectories first and then new ids from
+// the request's queue head: one atomic addition on the head per claim, and the in-flight count
+// raised by what was actually obtained (an addition nobody waits for).  The first pass keeps each
+// request within this CTA's share of its fair-share cap (counted in shared memory); the second
+// pass, unless caps are strict, has no cap, so no lane idles while any request has work.
 template <int T>
-__device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, int kind, int &n_active,
-                                       unsigned &cursor) {
+__device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, const CtaView &V, int kind,
+                                       int &n_active, unsigned &cursor) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     unsigned idle[T];
@@ -253,43 +326,40 @@ __device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, int kin
             unsigned long long base = 0;
             int got = 0, gp = 0;
             unsigned p0 = 0;
-            if (lane == 0) {
-                // Reserve in-flight places first (exact fair-share cap in the first pass), take
-                // suspended trajectories, then new ids from the queue head; unused reservations
-                // are given back.
+            if (lane == 0 && (V.ok[s] & 3u)) {
                 SlotCtl *C = E.ctl + s;
                 const unsigned long long n_traj = E.slots[s].n_traj;
-                if (vload(C->state) == kSlotActive &&
-                    (vload(C->head) < n_traj || vload(C->park_avail) > 0)) {
-                    int want = total;
-                    const int prev = atomicAdd(&C->inflight, want);
-                    if (pass == 0) {
-                        const int room = E.caps[s] - prev;
-                        const int allowed = room < 0 ? 0 : (room < want ? room : want);
-                        if (allowed < want) atomicSub(&C->inflight, want - allowed);
-                        want = allowed;
+                int want = total;
+                if (pass == 0) {
+                    const int cap = (E.caps[s] + static_cast<int>(gridDim.x) - 1) / static_cast<int>(gridDim.x);
+                    const int room = cap - V.held[s];
+                    want = room < 0 ? 0 : (room < want ? room : want);
+                }
+                if (want > 0 && (V.ok[s] & 2u)) {
+                    const int pv = atomicSub(&C->park_avail, want);
+                    if (pv <= 0) {
+                        atomicAdd(&C->park_avail, want);
+                        atomicAnd(&V.ok[s], ~2u);
+                    } else {
+                        gp = pv < want ? pv : want;
+                        if (gp < want) atomicAdd(&C->park_avail, want - gp);
+                        p0 = atomicAdd(&C->park_head, static_cast<unsigned>(gp));
+                        atomicSub(&C->park_used, gp);
                     }
-                    if (want > 0 && vload(C->park_avail) > 0) {
-                        const int pv = atomicSub(&C->park_avail, want);
-                        if (pv <= 0) {
-                            atomicAdd(&C->park_avail, want);
-                        } else {
-                            gp = pv < want ? pv : want;
-                            if (gp < want) atomicAdd(&C->park_avail, want - gp);
-                            p0 = atomicAdd(&C->park_head, static_cast<unsigned>(gp));
-                            atomicSub(&C->park_used, gp);
-                        }
+                }
+                got = gp;
+                if (want > gp && (V.ok[s] & 1u)) {
+                    const int wn = want - gp;
+                    base = atomicAdd(&C->head, static_cast<unsigned long long>(wn));
+                    if (base < n_traj) {
+                        const unsigned long long left = n_traj - base;
+                        got += left < static_cast<unsigned long long>(wn) ? static_cast<int>(left) : wn;
                     }
-                    got = gp;
-                    if (want > gp && vload(C->head) < n_traj) {
-                        const int wn = want - gp;
-                        base = atomicAdd(&C->head, static_cast<unsigned long long>(wn));
-                        if (base < n_traj) {
-                            const unsigned long long left = n_traj - base;
-                            got += left < static_cast<unsigned long long>(wn) ? static_cast<int>(left) : wn;
-                        }
-                    }
-                    if (got < want) atomicSub(&C->inflight, want - got);
+                    if (base + static_cast<unsigned long long>(wn) >= n_traj) atomicAnd(&V.ok[s], ~1u);
+                }
+                if (got) {
+                    atomicAdd(&C->inflight, got);
+                    atomicAdd(&V.held[s], got);
                 }
             }
             got = __shfl_sync(kFull, got, 0);
@@ -322,7 +392,8 @@ __device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, int kin
 // ramped) until the launch's block count is reached or the whole warp has run out of work.
 // Returns the next block index.
 template <int M, int H, int R, int T>
-__device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E, unsigned b, int &n_active,
+__device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E, const CtaView &V, unsigned b,
+                                               int &n_active,
                                unsigned &cursor, unsigned long long &useful, unsigned &n_esc,
                                unsigned &n_cens) {
     const unsigned nb = E.chunk_blocks;
@@ -392,8 +463,8 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
                     philox_lane_set_hi(L[t].P, L[t].c_hi - 1u, L[t].c_hi);
                 }
             }
-            finish_lanes(L, E, useful, n_active, n_esc, n_cens);
-            refill(L, E, kind_of(M, H, R), n_active, cursor);
+            finish_lanes(L, E, V, useful, n_active, n_esc, n_cens);
+            refill(L, E, V, kind_of(M, H, R), n_active, cursor);
             if (!__any_sync(kFull, n_active > 0)) break;
         }
     }
@@ -409,6 +480,28 @@ __global__ void __launch_bounds__(T == 1 ? 640 : 256, 1) engine_chunk_kernel(Eng
     const unsigned gtid = blockIdx.x * blockDim.x + threadIdx.x;
     const unsigned warp = gtid >> 5;
     const int lane = threadIdx.x & 31;
+    // This CTA's view of the requests for the launch: which listed requests have ids or suspended
+    // trajectories to hand out, and how many of its lanes hold each.
+    __shared__ unsigned sh_ok[kMaxRequests];
+    __shared__ int sh_held[kMaxRequests];
+    const CtaView V{sh_ok, sh_held};
+    for (int s = threadIdx.x; s < E.max_requests; s += blockDim.x) {
+        sh_ok[s] = 0u;
+        sh_held[s] = 0;
+    }
+    __syncthreads();
+    {
+        int listed = 0;
+        for (int k = 0; k < kNumKinds; ++k) listed += E.act_count[k];
+        for (int i = threadIdx.x; i < listed; i += blockDim.x) {
+            int k = 0, j = i;
+            while (j >= E.act_count[k]) j -= E.act_count[k++];
+            const int s = E.act_list[k * E.max_requests + j];
+            const SlotCtl &C = E.ctl[s];
+            if (vload(C.state) != kSlotActive) continue;
+            sh_ok[s] = (vload(C.head) < E.slots[s].n_traj ? 1u : 0u) | (vload(C.park_avail) > 0 ? 2u : 0u);
+        }
+    }
     Lane L[T];
     int n_active = 0;
 #pragma unroll
@@ -436,14 +529,16 @@ __global__ void __launch_bounds__(T == 1 ? 640 : 256, 1) engine_chunk_kernel(Eng
         L[t].esc = -1;
         load_consts(L[t], S);
         set_progress(L[t], S);
+        atomicAdd(&sh_held[s], 1);
         ++n_active;
     }
+    __syncthreads();
     int kind = E.warp_kind[warp];
     if (!__any_sync(kFull, n_active > 0)) kind = -1;
     unsigned cursor = E.warp_cursor[warp];
     unsigned long long useful = 0;
     unsigned n_esc = 0, n_cens = 0;
-    if (kind >= 0) refill(L, E, kind, n_active, cursor);
+    if (kind >= 0) refill(L, E, V, kind, n_active, cursor);
     unsigned b = 0;
     while (b < E.chunk_blocks) {
         if (kind < 0) {
@@ -451,7 +546,7 @@ __global__ void __launch_bounds__(T == 1 ? 640 : 256, 1) engine_chunk_kernel(Eng
             const int first = static_cast<int>(warp % kNumKinds);
             for (int q = 0; q < kNumKinds && kind < 0; ++q) {
                 const int m = (first + q) % kNumKinds;
-                refill(L, E, m, n_active, cursor);
+                refill(L, E, V, m, n_active, cursor);
                 if (__any_sync(kFull, n_active > 0)) kind = m;
             }
             if (kind < 0) break;
@@ -459,7 +554,7 @@ __global__ void __launch_bounds__(T == 1 ? 640 : 256, 1) engine_chunk_kernel(Eng
         switch (kind) {
 #define FPT_KIND_CASE(M_, H_, R_)                                                              \
     case kind_of(M_, H_, R_):                                                                \
-        b = run_blocks<M_, H_, R_, T>(L, E, b, n_active, cursor, useful, n_esc, n_cens);       \
+        b = run_blocks<M_, H_, R_, T>(L, E, V, b, n_active, cursor, useful, n_esc, n_cens);    \
         break;
         FPT_KIND_CASE(kUnder, kEuler, kConstBias)
         FPT_KIND_CASE(kOver, kEuler, kConstBias)
@@ -469,7 +564,7 @@ __global__ void __launch_bounds__(T == 1 ? 640 : 256, 1) engine_chunk_kernel(Eng
         FPT_KIND_CASE(kOver, kEuler, kRamp)
         FPT_KIND_CASE(kUnder, kHeun, kRamp)
         default:
-            b = run_blocks<kOver, kHeun, kRamp, T>(L, E, b, n_active, cursor, useful, n_esc, n_cens);
+            b = run_blocks<kOver, kHeun, kRamp, T>(L, E, V, b, n_active, cursor, useful, n_esc, n_cens);
             break;
 #undef FPT_KIND_CASE
         }
@@ -548,6 +643,16 @@ __device__ __forceinline__ double u128_to_d(unsigned long long lo, unsigned long
                      static_cast<double>(lo));
 }
 
+// lo:hi (128 bits) += l0 + 2^32 l1 + 2^64 l2, exactly (l0, l1, l2 < 2^64).
+__device__ __forceinline__ void add_limbs(unsigned long long &lo, unsigned long long &hi, unsigned long long l0,
+                                          unsigned long long l1, unsigned long long l2) {
+    const unsigned long long a = l1 << 32, ah = l1 >> 32;   // 2^32 l1 = ah:a
+    lo += l0;
+    hi += lo < l0 ? 1ull : 0ull;
+    lo += a;
+    hi += ah + (lo < a ? 1ull : 0ull) + l2;
+}
+
 // Fold completed id blocks, in id order, into each request's running sums; stop at the first
 // prefix meeting the relative-standard-error rule, or when every block is complete.
 __global__ void engine_scan_kernel(EngineDev E) {
@@ -571,10 +676,8 @@ __global__ void engine_scan_kernel(EngineDev E) {
         C->n_esc += A.escaped;
         C->under += A.under;
         C->over += A.over;
-        C->s1_lo += A.s1_lo;
-        C->s1_hi += A.s1_hi + (C->s1_lo < A.s1_lo ? 1ull : 0ull);
-        C->s2_lo += A.s2_lo;
-        C->s2_hi += A.s2_hi + (C->s2_lo < A.s2_lo ? 1ull : 0ull);
+        add_limbs(C->s1_lo, C->s1_hi, A.s1[0], A.s1[1], 0ull);
+        add_limbs(C->s2_lo, C->s2_hi, A.s2[0], A.s2[1], A.s2[2]);
         ++p;
         if (S->stop_rse > 0.0 && C->n_esc >= 2) {
             const double n = static_cast<double>(C->n_esc);
