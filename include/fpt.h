@@ -158,6 +158,9 @@ typedef struct {
     uint32_t resident_requests, pending_requests;
     double kernel_ms;           /* summed device time of the resident-kernel launches (CUDA events) */
     uint64_t preempted;         /* lane suspensions ordered so starved requests get their share */
+    uint64_t check_flags;       /* bounds-checked build (FPT_CHECK): one bit per kind of index
+                                   found out of range (the access was skipped); 0 otherwise and
+                                   always 0 in the regular build */
 } fpt_engine_counters;
 
 /* Create an engine on config->device (NULL config = defaults). */
@@ -244,12 +247,15 @@ const char *fpt_status_string(fpt_status s);
  *
  * Scratch: a fixed 8 MiB __device__ array inside the library (every GPU that loads the library
  * holds it until the process exits): a queue head, a finished-CTA counter and one record of
- * partial sums and per-bin counts per CTA.  Requests whose records do not fit (many histogram
- * bins: roughly bins > 8 MiB / (4 x CTAs), or bins > 10240) are rejected with FPT_EINVAL and a
- * message giving the limit.  The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call before any stream
- * capture.  Every call shares the array: the header is cleared on `stream` before each launch,
- * and calls that overlap on the GPU (other streams, other threads) race on it.
+ * partial sums and per-bin counts per CTA.  With many histogram bins the launch uses as many
+ * CTAs as have room for their record (fewer CTAs, same result); hist_bins is limited to 10240
+ * (the per-CTA histogram lives in shared memory) and n_traj to 2^32 - 1 (32-bit per-CTA bin
+ * counts); larger requests are rejected with FPT_EINVAL and a message giving the limit.  The
+ * first call on each device (and the first after that device's context changed, e.g. after
+ * cudaDeviceReset) looks up the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  Every call shares the array: the
+ * header is cleared on `stream` before each launch, and calls that overlap on the GPU (other
+ * streams, other threads) race on it.
  *
  * Arguments: params as for the engine but stop_rse must be 0; trajectories params->traj_offset
  * .. +n_traj-1 of `seed`.  d_steps (device, n_traj int64, may be NULL) receives each escape step

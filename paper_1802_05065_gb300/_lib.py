@@ -11,7 +11,8 @@ import math
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "_build", "libfpt_gb300.so")
+# FPT_LIBRARY selects another build of the same library (e.g. _build/libfpt_gb300_check.so)
+LIB_PATH = os.environ.get("FPT_LIBRARY") or os.path.join(HERE, "_build", "libfpt_gb300.so")
 SELFTEST_PATH = os.path.join(HERE, "_build", "libfpt_selftest.so")
 
 OK, PENDING, EINVAL, ENOMEM, EBUSY, ENOTFOUND, ETIMEDOUT, ECUDA, EFULL = 0, 1, -1, -2, -3, -4, -5, -6, -7
@@ -78,7 +79,7 @@ class EngineCounters(ctypes.Structure):
         ("block", ctypes.c_uint32), ("traj_per_thread", ctypes.c_uint32),
         ("chunk_steps", ctypes.c_uint32), ("resident_requests", ctypes.c_uint32),
         ("pending_requests", ctypes.c_uint32), ("kernel_ms", ctypes.c_double),
-        ("preempted", ctypes.c_uint64),
+        ("preempted", ctypes.c_uint64), ("check_flags", ctypes.c_uint64),
     ]
 
     def as_dict(self) -> dict:

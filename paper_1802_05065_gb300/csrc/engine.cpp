@@ -86,7 +86,7 @@ struct CkptHeader {
     uint64_t n_park, has_per_traj;
 };
 constexpr uint64_t kCkptMagic = 0x5450464B43505446ull;   // "FTPCKFPT"
-constexpr uint64_t kCkptVersion = 3;   // 3: id-block sums kept as 32-bit limbs
+constexpr uint64_t kCkptVersion = 3;   // 3: id-block sums as 32-bit limbs, histogram rows per hist_rows
 
 // Ring of suspended trajectories: never more than the lanes can hold twice over.
 uint32_t park_capacity(uint64_t n_traj, unsigned lanes) {
@@ -94,9 +94,17 @@ uint32_t park_capacity(uint64_t n_traj, unsigned lanes) {
     return static_cast<uint32_t>(std::max<uint64_t>(cap, 1));
 }
 
+// Histogram rows of a request: one per id block when the prefix stop rule may cut the result
+// (the result's histogram is the sum of the rows of its prefix), otherwise one per 2^31 ids
+// (32-bit counts cannot overflow) -- a single row up to 2^31 trajectories.
+uint64_t hist_rows(const fpt_params &p, uint64_t n_traj, uint32_t B) {
+    if (p.stop_rse > 0.0) return (n_traj + B - 1) / B;
+    return (n_traj + kHistRowIds - 1) / kHistRowIds;
+}
+
 size_t request_bytes(const fpt_params &p, uint64_t n_traj, uint32_t B, unsigned lanes) {
     const uint64_t nb = (n_traj + B - 1) / B;
-    size_t bytes = nb * sizeof(IdBlockAcc) + nb * static_cast<size_t>(p.hist_bins) * 4;
+    size_t bytes = nb * sizeof(IdBlockAcc) + hist_rows(p, n_traj, B) * static_cast<size_t>(p.hist_bins) * 4;
     bytes += static_cast<size_t>(park_capacity(n_traj, lanes)) * sizeof(ParkEntry);
     if (p.keep_per_traj) bytes += n_traj * 8;
     return bytes;
@@ -223,9 +231,10 @@ fpt_status admit(fpt_engine *e) {
         }
         const uint64_t nb = R.n_idblocks;
         CK(cudaMalloc(&R.acc, nb * sizeof(IdBlockAcc)));
-        CK(cudaMalloc(&R.hist, nb * static_cast<size_t>(R.params.hist_bins) * 4));
+        const size_t hist_bytes = hist_rows(R.params, R.n_traj, R.stop_block) * static_cast<size_t>(R.params.hist_bins) * 4;
+        CK(cudaMalloc(&R.hist, hist_bytes));
         CK(cudaMemsetAsync(R.acc, 0, nb * sizeof(IdBlockAcc), e->stream));
-        CK(cudaMemsetAsync(R.hist, 0, nb * static_cast<size_t>(R.params.hist_bins) * 4, e->stream));
+        CK(cudaMemsetAsync(R.hist, 0, hist_bytes, e->stream));
         if (R.params.keep_per_traj) {
             CK(cudaMalloc(&R.per_traj, R.n_traj * 8));
             CK(cudaMemsetAsync(R.per_traj, 0xFF, R.n_traj * 8, e->stream));
@@ -267,6 +276,8 @@ fpt_status admit(fpt_engine *e) {
         S.n_idblocks = R.n_idblocks;
         S.acc = R.acc;
         S.hist = R.hist;
+        S.hist_per_block = R.params.stop_rse > 0.0 ? 1 : 0;
+        S.hist_rows = static_cast<uint32_t>(hist_rows(R.params, R.n_traj, R.stop_block));
         S.per_traj = R.per_traj;
         S.park = R.park;
         S.park_cap = R.park_cap;
@@ -281,7 +292,7 @@ fpt_status admit(fpt_engine *e) {
             q += sizeof(CkptHeader);
             std::memcpy(&C, q, sizeof(SlotCtl));
             q += sizeof(SlotCtl);
-            const size_t acc_b = nb * sizeof(IdBlockAcc), hist_b = nb * static_cast<size_t>(R.params.hist_bins) * 4;
+            const size_t acc_b = nb * sizeof(IdBlockAcc), hist_b = hist_bytes;
             CK(cudaMemcpyAsync(R.acc, q, acc_b, cudaMemcpyHostToDevice, e->stream));
             q += acc_b;
             CK(cudaMemcpyAsync(R.hist, q, hist_b, cudaMemcpyHostToDevice, e->stream));
@@ -744,6 +755,7 @@ fpt_status create_impl(const fpt_engine_config *cfg_in, fpt_engine *e) {
     d.counters = e->d_counters;
     d.chunk_blocks = e->chunk_blocks;
     d.max_requests = R;
+    d.n_lanes = e->lanes;
     CK(cudaStreamSynchronize(e->stream));
     if (cfg.use_graph)
         for (IterIO &B : e->iters) {
@@ -890,7 +902,9 @@ extern "C" fpt_status fpt_histogram(fpt_engine *e, uint64_t req_id, uint64_t *co
         if (!R) return fail(e, FPT_ENOTFOUND, "unknown request id");
         if (R->phase != kFinished) return fail(e, FPT_PENDING, "request not finished");
         if (nbins != R->params.hist_bins) return fail(e, FPT_EINVAL, "nbins != params.hist_bins");
-        prefix = R->prefix;
+        // rows of the result: the id blocks of the prefix, or every row without a stop rule
+        prefix = R->params.stop_rse > 0.0 ? R->prefix
+                                          : static_cast<unsigned>(hist_rows(R->params, R->n_traj, R->stop_block));
         hist = R->hist;
         if (under) *under = R->sums.under;
         if (over) *over = R->sums.over;
@@ -963,7 +977,7 @@ extern "C" fpt_status fpt_per_traj_steps(fpt_engine *e, uint64_t req_id, int64_t
 // per-trajectory steps (if kept) and at most the ring's capacity of suspended trajectories.
 static size_t ckpt_bound(const Request &R, unsigned lanes) {
     size_t b = sizeof(CkptHeader) + sizeof(SlotCtl) + R.n_idblocks * sizeof(IdBlockAcc) +
-               static_cast<size_t>(R.n_idblocks) * R.params.hist_bins * 4 +
+               hist_rows(R.params, R.n_traj, R.stop_block) * R.params.hist_bins * 4 +
                static_cast<size_t>(park_capacity(R.n_traj, lanes)) * sizeof(ParkEntry);
     if (R.params.keep_per_traj) b += R.n_traj * 8;
     return b;
@@ -1032,7 +1046,8 @@ extern "C" fpt_status fpt_checkpoint(fpt_engine *e, uint64_t req_id, void *buf, 
         CK(cudaMemcpy(&C, e->d_ctl + R->slot, sizeof(SlotCtl), cudaMemcpyDeviceToHost));
         H.n_park = C.park_tail - C.park_head;
     }
-    const size_t nb = R->n_idblocks, hist_b = nb * static_cast<size_t>(R->params.hist_bins) * 4;
+    const size_t nb = R->n_idblocks,
+                 hist_b = hist_rows(R->params, R->n_traj, R->stop_block) * static_cast<size_t>(R->params.hist_bins) * 4;
     std::memcpy(q, &H, sizeof(H));
     q += sizeof(H);
     std::memcpy(q, &C, sizeof(C));
@@ -1093,7 +1108,7 @@ extern "C" fpt_status fpt_restore(fpt_engine *e, const void *buf, size_t size, u
         return fail(e, FPT_EINVAL, "checkpoint header is inconsistent");
     const size_t nb = H.n_idblocks;
     const size_t want = sizeof(CkptHeader) + sizeof(SlotCtl) + nb * sizeof(IdBlockAcc) +
-                        nb * static_cast<size_t>(H.params.hist_bins) * 4 +
+                        hist_rows(H.params, H.n_traj, B) * static_cast<size_t>(H.params.hist_bins) * 4 +
                         (H.has_per_traj ? H.n_traj * 8 : 0) + H.n_park * sizeof(ParkEntry);
     if (size != want) return fail(e, FPT_EINVAL, "checkpoint size does not match its header");
     if (H.n_park > park_capacity(H.n_traj, e->lanes))
@@ -1141,6 +1156,7 @@ extern "C" fpt_status fpt_get_counters(fpt_engine *e, fpt_engine_counters *out) 
     out->useful_steps = e->h_counters[kCntUseful];
     out->escapes = e->h_counters[kCntEscapes];
     out->censored = e->h_counters[kCntCensored];
+    out->check_flags = e->h_counters[kCntCheck];
     out->lane_step_slots = e->iterations * static_cast<uint64_t>(e->lanes) * e->chunk_blocks * kBlockSteps;
     out->lanes = e->lanes;
     out->grid = e->grid;

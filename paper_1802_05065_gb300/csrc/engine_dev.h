@@ -8,8 +8,8 @@
 //       r (wrapped phase), v, hb (upper event bound), w (winding), c (64-bit Philox block
 //       counter = Philox blocks of 4 steps consumed, a multiple of kBlockPhilox between kernel
 //       blocks), gid (64-bit trajectory id), slot, budget
-//   per request: IdBlockAcc[n_idblocks] + u32 histogram rows [n_idblocks][hist_bins]
-//       (+ optional int64 escape step per trajectory)
+//   per request: IdBlockAcc[n_idblocks] + u32 histogram rows [rows][hist_bins], rows = n_idblocks
+//       with a stop rule, ceil(n_traj / 2^31) without (+ optional int64 escape step per trajectory)
 #pragma once
 
 #include <cstdint>
@@ -30,6 +30,10 @@ constexpr int kMaxRequests = 1024;
 // c_base the trajectory's own block count rounded down to a multiple of kRebaseBlocks, so the
 // rounding depends only on the trajectory's step count, never on scheduling.
 constexpr unsigned kRebaseBlocks = 1u << 20;
+
+// Trajectory ids per histogram row of a request without a stop rule (its 32-bit counts cannot
+// overflow); with a stop rule there is one row per id block.
+constexpr uint64_t kHistRowIds = 1ull << 31;
 
 // A trajectory suspended by preemption: everything needed to continue it exactly.
 struct ParkEntry {
@@ -64,7 +68,9 @@ struct SlotDev {
     double stop_rse;
     uint32_t stop_block, n_idblocks;
     IdBlockAcc *acc;
-    unsigned int *hist;
+    unsigned int *hist;        // rows x hist_bins
+    int32_t hist_per_block;    // 1: row = id block (stop rule), 0: row = id / kHistRowIds
+    uint32_t hist_rows;
     long long *per_traj;
     ParkEntry *park;           // ring of suspended trajectories
     unsigned park_cap;
@@ -90,7 +96,9 @@ struct LaneSoA {
     unsigned int *c_lo, *c_hi, *gid_lo, *gid_hi, *budget;
 };
 
-enum : int { kCntUseful = 0, kCntEscapes = 1, kCntCensored = 2, kCntCount = 4 };
+// Global counters; kCntCheck collects the violated bounds of a build with FPT_CHECK (bit per
+// check, see engine_kernels.cu), 0 otherwise.
+enum : int { kCntUseful = 0, kCntEscapes = 1, kCntCensored = 2, kCntCheck = 3, kCntCount = 4 };
 
 struct EngineDev {
     SlotDev *slots;
@@ -109,6 +117,7 @@ struct EngineDev {
     unsigned long long *counters;
     unsigned int chunk_blocks;
     int max_requests;
+    unsigned int n_lanes;   // threads x trajectories per thread (lane state entries)
 };
 
 }  // namespace fpt

@@ -44,6 +44,28 @@ struct Lane {
 
 __device__ __forceinline__ float qnan_f() { return __int_as_float(0x7FFFFFFF); }
 
+// Bounds checks of the FPT_CHECK build: a violated one sets its bit in the global check word
+// (counters[kCntCheck], read back with the engine counters) and the access is skipped; nothing
+// traps.  In the regular build every check is `true`.
+enum : unsigned {
+    kChkSlot = 0,      // request slot outside [0, max_requests)
+    kChkLane = 1,      // lane-state index outside [0, n_lanes)
+    kChkIdBlock = 2,   // id block outside [0, n_idblocks)
+    kChkHistRow = 3,   // histogram row outside [0, hist_rows)
+    kChkBin = 4,       // histogram bin outside [0, hist_bins)
+    kChkTraj = 5,      // trajectory index outside [0, n_traj)
+    kChkPark = 6,      // suspended-trajectory ring index outside [0, park_cap)
+    kChkKind = 7,      // kind outside [0, kNumKinds)
+};
+#ifdef FPT_CHECK
+__device__ __forceinline__ bool checked(const EngineDev &E, bool ok, unsigned bit) {
+    if (!ok) atomicOr(&E.counters[kCntCheck], 1ull << bit);
+    return ok;
+}
+#else
+__device__ __forceinline__ constexpr bool checked(const EngineDev &, bool, unsigned) { return true; }
+#endif
+
 template <typename V>
 __device__ __forceinline__ V vload(const V &x) {
     return *const_cast<const volatile V *>(&x);
@@ -170,27 +192,33 @@ __device__ __forceinline__ void emit_warp(const EngineDev &E, const CtaView &V, 
     const int lane = threadIdx.x & 31;
     const SlotDev *S = E.slots + (fin ? slot : 0);
     unsigned long long idx = 0;
-    unsigned ib = 0;
+    unsigned ib = 0, row = 0;
     int bin = -2;
     if (fin) {
         idx = gid - S->traj_offset;
         ib = static_cast<unsigned>(idx / S->stop_block);
+        row = S->hist_per_block ? ib : static_cast<unsigned>(idx / kHistRowIds);
         if (escaped) bin = hist_bin(S, k);
-        if (S->per_traj) S->per_traj[idx] = escaped ? static_cast<long long>(k) : -1ll;
+        // an index out of range (checked build only) drops the trajectory's result
+        fin = checked(E, slot >= 0 && slot < E.max_requests, kChkSlot) &&
+              checked(E, idx < S->n_traj, kChkTraj) && checked(E, ib < S->n_idblocks, kChkIdBlock) &&
+              checked(E, row < S->hist_rows, kChkHistRow) &&
+              checked(E, bin == -2 || (bin >= -1 && bin <= S->hist_bins), kChkBin);
+        if (fin && S->per_traj) S->per_traj[idx] = escaped ? static_cast<long long>(k) : -1ll;
     }
-    // slot < 2^10, id block < 2^32, bin < 2^21: distinct keys for distinct groups
+    // slot < 2^10, id block and row < 2^32, bin < 2^21: distinct keys for distinct groups
     const unsigned long long gkey = fin ? (static_cast<unsigned long long>(slot) << 32) | ib : ~0ull;
     const unsigned grp = __match_any_sync(kFull, gkey);
     const unsigned long long bkey =
         fin && bin >= 0 && bin < S->hist_bins
-            ? (static_cast<unsigned long long>(slot) << 53) | (static_cast<unsigned long long>(ib) << 21) |
+            ? (static_cast<unsigned long long>(slot) << 53) | (static_cast<unsigned long long>(row) << 21) |
                   static_cast<unsigned long long>(bin)
             : ~0ull;
     const unsigned bgrp = __match_any_sync(kFull, bkey);
     if (!fin) return;
     IdBlockAcc *A = S->acc + ib;
     if (bkey != ~0ull && lane == __ffs(bgrp) - 1)
-        atomicAdd(S->hist + static_cast<size_t>(ib) * S->hist_bins + bin, static_cast<unsigned>(__popc(bgrp)));
+        atomicAdd(S->hist + static_cast<size_t>(row) * S->hist_bins + bin, static_cast<unsigned>(__popc(bgrp)));
     // limbs: k = k0 + 2^32 k1, k^2 = q0 + 2^32 q1 + 2^64 q2 (each < 2^32)
     const unsigned long long kk_lo = escaped ? k * k : 0ull, kk_hi = escaped ? __umul64hi(k, k) : 0ull;
     const unsigned long long ke = escaped ? k : 0ull;
@@ -315,6 +343,7 @@ __device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, const C
     }
     if (total == 0) return;
     if (static_cast<int>(threadIdx.x >> 5) >= *E.claim_warps) return;   // spread scarce work
+    if (!checked(E, kind >= 0 && kind < kNumKinds, kChkKind)) return;
     const int cnt = E.act_count[kind];
     if (cnt <= 0) return;
     const int *list = E.act_list + kind * E.max_requests;
@@ -323,6 +352,7 @@ __device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, const C
         for (int scanned = 0; scanned < cnt && total > 0; ++scanned) {
             const int s = list[cursor % static_cast<unsigned>(cnt)];
             ++cursor;
+            if (!checked(E, s >= 0 && s < E.max_requests, kChkSlot)) continue;
             unsigned long long base = 0;
             int got = 0, gp = 0;
             unsigned p0 = 0;
@@ -374,8 +404,10 @@ __device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, const C
                 const unsigned m = idle[t];
                 const int rank = before + __popc(m & lt);
                 if (((m >> lane) & 1u) && rank < got) {
-                    if (rank < gp)
-                        resume_lane(L[t], E, s, S->park[(p0 + static_cast<unsigned>(rank)) % S->park_cap]);
+                    if (rank < gp) {
+                        const unsigned pi = (p0 + static_cast<unsigned>(rank)) % S->park_cap;
+                        if (checked(E, pi < S->park_cap, kChkPark)) resume_lane(L[t], E, s, S->park[pi]);
+                    }
                     else
                         init_lane(L[t], E, s, base + static_cast<unsigned long long>(rank - gp));
                     ++n_active;
@@ -507,7 +539,8 @@ __global__ void __launch_bounds__(T == 1 ? 640 : 256, 1) engine_chunk_kernel(Eng
 #pragma unroll
     for (int t = 0; t < T; ++t) {
         const unsigned i = t * nthreads + gtid;
-        int s = E.lanes.slot[i];
+        int s = checked(E, i < E.n_lanes, kChkLane) ? E.lanes.slot[i] : -1;
+        if (s >= 0 && !checked(E, s < E.max_requests, kChkSlot)) s = -1;
         if (s >= 0 && vload(E.ctl[s].state) != kSlotActive) {   // request finished or cancelled
             atomicSub(&E.ctl[s].inflight, 1);
             s = -1;
@@ -534,6 +567,7 @@ __global__ void __launch_bounds__(T == 1 ? 640 : 256, 1) engine_chunk_kernel(Eng
     }
     __syncthreads();
     int kind = E.warp_kind[warp];
+    if (kind >= 0 && !checked(E, kind < kNumKinds, kChkKind)) kind = -1;
     if (!__any_sync(kFull, n_active > 0)) kind = -1;
     unsigned cursor = E.warp_cursor[warp];
     unsigned long long useful = 0;
@@ -593,6 +627,7 @@ __global__ void __launch_bounds__(T == 1 ? 640 : 256, 1) engine_chunk_kernel(Eng
             continue;
         }
         const unsigned pi = atomicAdd(&C->park_tail, 1u);
+        if (!checked(E, pi % S->park_cap < S->park_cap, kChkPark)) continue;
         ParkEntry &P = S->park[pi % S->park_cap];
         P.r = L[t].r;
         P.v = L[t].v;
@@ -610,6 +645,7 @@ __global__ void __launch_bounds__(T == 1 ? 640 : 256, 1) engine_chunk_kernel(Eng
 #pragma unroll
     for (int t = 0; t < T; ++t) {
         const unsigned i = t * nthreads + gtid;
+        if (!checked(E, i < E.n_lanes, kChkLane)) continue;
         E.lanes.slot[i] = L[t].slot;
         if (L[t].slot < 0) continue;
         E.lanes.r[i] = L[t].r;

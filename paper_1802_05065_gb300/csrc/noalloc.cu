@@ -11,7 +11,8 @@
 //
 // Scratch: kNoAllocScratchBytes (8 MiB) in a file-scope __device__ array, held by every GPU
 // that loads the library until the process exits.  Layout: a 256-byte header (queue head,
-// finished-CTA counter), then one record per CTA (exact partial sums + per-bin counts).
+// finished-CTA counter), then one record per CTA (exact partial sums + per-bin counts).  When
+// the records of a full grid do not fit (many histogram bins) the launch uses fewer CTAs.
 // Every call shares the array and it keeps the previous call's contents; the header is cleared
 // on the stream before each launch.  Calls that overlap on the GPU race on it.
 #include <cstdint>
@@ -247,9 +248,34 @@ __global__ void __launch_bounds__(kBlock) noalloc_kernel(NoAllocArgs a) {
     }
 }
 
-// Device address of the scratch array, looked up once per device (with that device current).
+// The current CUDA context's handle, through the driver entry point the runtime exposes (the
+// library does not link the driver library itself); nullptr if it cannot be had.
+using CtxGetCurrentFn = int (*)(void **);   // cuCtxGetCurrent(CUcontext *)
+void *current_context() {
+    static CtxGetCurrentFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<CtxGetCurrentFn>(p);
+    });
+    void *ctx = nullptr;
+    if (fn && fn(&ctx) != 0) ctx = nullptr;
+    return ctx;
+}
+
+// Device address of the scratch array: set up once per device, with that device current, and
+// set up again if the device's context has changed since (after cudaDeviceReset the module is
+// loaded anew and the array may live at another address).
 std::mutex g_sym_mu;
-void *g_sym_ptr[64] = {};
+struct SymEntry {
+    void *ptr = nullptr;
+    void *ctx = nullptr;
+};
+SymEntry g_sym[64];
 
 fpt_status scratch_address(int dev, unsigned char **out) {
     std::lock_guard<std::mutex> lk(g_sym_mu);
@@ -257,16 +283,18 @@ fpt_status scratch_address(int dev, unsigned char **out) {
         set_error("device ordinal out of range for the no-alloc scratch table");
         return FPT_EINVAL;
     }
-    if (!g_sym_ptr[dev]) {
+    void *ctx = current_context();
+    if (!g_sym[dev].ptr || g_sym[dev].ctx != ctx) {
         void *p = nullptr;
         const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess || !p) {
             set_error(std::string("cudaGetSymbolAddress(no-alloc scratch): ") + cudaGetErrorString(e));
             return FPT_ECUDA;
         }
-        g_sym_ptr[dev] = p;
+        g_sym[dev].ptr = p;
+        g_sym[dev].ctx = ctx;
     }
-    *out = static_cast<unsigned char *>(g_sym_ptr[dev]);
+    *out = static_cast<unsigned char *>(g_sym[dev].ptr);
     return FPT_OK;
 }
 
@@ -296,8 +324,8 @@ extern "C" fpt_status fpt_run_noalloc(const fpt_params *params, uint64_t n_traj,
         set_error("d_sums and d_hist are required device outputs");
         return FPT_EINVAL;
     }
-    if (n_traj > (1ull << 40)) {
-        set_error("n_traj must be <= 2^40");
+    if (n_traj > 0xFFFFFFFFull) {   // a CTA's per-bin counts are 32-bit
+        set_error("fpt_run_noalloc: n_traj must be < 2^32");
         return FPT_EINVAL;
     }
     if (n_traj == 0) return FPT_OK;
@@ -336,16 +364,17 @@ extern "C" fpt_status fpt_run_noalloc(const fpt_params *params, uint64_t n_traj,
     unsigned grid = static_cast<unsigned>(sms * per_sm);
     const uint64_t lanes_needed = (n_traj + kBlock - 1) / kBlock;
     if (grid > lanes_needed) grid = static_cast<unsigned>(lanes_needed);
+    // one record per CTA must fit in the fixed scratch: with many bins, run fewer CTAs (the
+    // lanes claim trajectories from one queue, so any grid computes the same result)
     const size_t rec = (64 + shmem + 255) / 256 * 256;
-    const size_t need = kHeaderBytes + static_cast<size_t>(grid) * rec;
-    if (need > kNoAllocScratchBytes) {
-        const size_t max_bins = ((kNoAllocScratchBytes - kHeaderBytes) / grid / 256 * 256 - 64) / 4;
+    const size_t fit = (kNoAllocScratchBytes - kHeaderBytes) / rec;
+    if (fit < 1) {
         set_error("fpt_run_noalloc: hist_bins = " + std::to_string(d.hist_bins) + " needs " +
-                  std::to_string(need) + " bytes of scratch, the fixed scratch holds " +
-                  std::to_string(kNoAllocScratchBytes) + " (at most " + std::to_string(max_bins) +
-                  " bins on this device)");
+                  std::to_string(kHeaderBytes + rec) + " bytes of scratch for one CTA, the fixed "
+                  "scratch holds " + std::to_string(kNoAllocScratchBytes));
         return FPT_EINVAL;
     }
+    if (grid > fit) grid = static_cast<unsigned>(fit);
     unsigned char *scratch = nullptr;
     const fpt_status st = scratch_address(dev, &scratch);
     if (st != FPT_OK) return st;

@@ -47,6 +47,16 @@ def test_exports_every_declared_symbol(lib):
     assert set(_lib.EXPORTS) <= declared
 
 
+def test_checked_build_exports_the_same_symbols(lib):
+    """The bounds-checked build (FPT_CHECK) is the same library with a checked resident kernel."""
+    import ctypes
+
+    from paper_1802_05065_gb300 import build as b
+    b.build()
+    C = ctypes.CDLL(b.LIB_CHECK)
+    for name in _declared():
+        assert hasattr(C, name), f"{name} missing from the checked build"
+
 def test_sums_finish_matches_oracle_stats(lib):
     rng = np.random.default_rng(1)
     for output in ("time", "bias"):
