@@ -17,8 +17,8 @@
 //
 // A warp integrates one kind at a time (model x integrator x constant or ramped bias: eight
 // code paths); the request of each lane is free, so requests of the same kind share warps.
-// Refill is round-robin over the claimable requests with a fair-share cap on in-flight lanes
-// per request (first pass), then without cap (second pass), so no lane idles while any request
+// Refill is round-robin over the claimable requests; while some request is starved, each is
+// kept within a fair-share cap on the lanes it holds, otherwise no lane idles while any request
 // has work.
 #include <cstdint>
 
@@ -326,9 +326,10 @@ __device__ __forceinline__ void finish_lanes(Lane (&L)[T], const EngineDev &E, c
 // Warp-collective refill of idle lanes with trajectories of requests of kind `kind`.  Lane 0
 // takes, per request in round-robin order, suspended trajectories first and then new ids from
 // the request's queue head: one atomic addition on the head per claim, and the in-flight count
-// raised by what was actually obtained (an addition nobody waits for).  The first pass keeps each
-// request within this CTA's share of its fair-share cap (counted in shared memory); the second
-// pass, unless caps are strict, has no cap, so no lane idles while any request has work.
+// raised by what was actually obtained (an addition nobody waits for).  While some request is
+// starved (strict caps, set by the host with preemption orders) each request is kept within
+// this CTA's share of its fair-share cap, counted in shared memory; otherwise lanes take work
+// from the first request that has some, so no lane idles while any request has work.
 template <int T>
 __device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, const CtaView &V, int kind,
                                        int &n_active, unsigned &cursor) {
@@ -347,8 +348,8 @@ __device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, const C
     const int cnt = E.act_count[kind];
     if (cnt <= 0) return;
     const int *list = E.act_list + kind * E.max_requests;
-    const int passes = *E.strict ? 1 : 2;
-    for (int pass = 0; pass < passes && total > 0; ++pass) {
+    const bool capped = *E.strict != 0;
+    {
         for (int scanned = 0; scanned < cnt && total > 0; ++scanned) {
             const int s = list[cursor % static_cast<unsigned>(cnt)];
             ++cursor;
@@ -360,7 +361,7 @@ __device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, const C
                 SlotCtl *C = E.ctl + s;
                 const unsigned long long n_traj = E.slots[s].n_traj;
                 int want = total;
-                if (pass == 0) {
+                if (capped) {
                     const int cap = (E.caps[s] + static_cast<int>(gridDim.x) - 1) / static_cast<int>(gridDim.x);
                     const int room = cap - V.held[s];
                     want = room < 0 ? 0 : (room < want ? room : want);
