@@ -283,6 +283,33 @@ fpt_status fpt_philox_fill(uint64_t seed, uint64_t traj, uint64_t block0, uint64
 fpt_status fpt_normals_fill(int precision, uint64_t seed, uint64_t traj, uint64_t n0, uint64_t n,
                             double *d_out, void *stream);
 
+/* ------------------------------------------------------------------------------------------
+ * Paper units (Sec. II.A, Eq. JJn).  The paper writes the junction as
+ *     phi'' + beta phi' = V0 (-sin phi + gamma + gamma_N),  <gamma_N gamma_N> = 2 D delta,
+ *     D = beta theta,
+ * in time units hbar / E_C, integrated with step h and bias increment delta_gamma per step
+ * (Alg. 1, Alg. 3).  Rescaling time by sqrt(V0) maps it onto the engine's plasma-frequency units:
+ *     alpha = beta / sqrt(V0),  D' = theta / V0 (= k_B T / E_J),  dt = sqrt(V0) h,
+ *     nu = delta_gamma / dt  (bias per unit engine time),
+ * with the fluctuation-dissipation noise sqrt(2 alpha D' dt) of fpt_params.  Host-only
+ * arithmetic in IEEE double; outputs are host pointers; FPT_EINVAL for non-positive V0, h, dt
+ * or non-finite arguments.
+ * ------------------------------------------------------------------------------------------ */
+fpt_status fpt_from_paper_units(double V0, double beta, double theta, double h, double delta_gamma,
+                                double *alpha, double *D, double *dt, double *nu);
+/* The inverse, for a chosen V0. */
+fpt_status fpt_to_paper_units(double alpha, double D, double dt, double nu, double V0,
+                              double *beta, double *theta, double *h, double *delta_gamma);
+/* A physical junction (R ohm, C farad, Ic ampere, T kelvin) in the paper's units (Sec. II.A
+ * normalisation): V0 = E_J / E_C, beta = hbar / (R (2e)^2), theta = k_B T / E_C, and the paper's
+ * time unit hbar / E_C in seconds, with E_J = hbar Ic / 2e and E_C = (2e)^2 / C. */
+fpt_status fpt_junction_paper_units(double R, double C, double Ic, double T, double *V0,
+                                    double *beta, double *theta, double *time_unit_s);
+/* Bias increment per step of a triangular bias sweep at sweep_hz that covers `span` of the
+ * critical current in half a period, with step h in units of time_unit_s (Sec. IV.B, Fig. 10b). */
+fpt_status fpt_sweep_delta_gamma(double sweep_hz, double h, double time_unit_s, double span,
+                                 double *delta_gamma);
+
 /* Library version string. */
 const char *fpt_version(void);
 

@@ -92,7 +92,8 @@ EXPORTS = [
     "fpt_release", "fpt_get_counters", "fpt_engine_stream", "fpt_destroy", "fpt_last_error",
     "fpt_status_string", "fpt_philox_fill", "fpt_normals_fill", "fpt_version",
     "fpt_request_sums", "fpt_run_noalloc", "fpt_checkpoint", "fpt_restore",
-    "fpt_engine_occupancy",
+    "fpt_engine_occupancy", "fpt_from_paper_units", "fpt_to_paper_units",
+    "fpt_junction_paper_units", "fpt_sweep_delta_gamma",
 ]
 
 _lib = None
@@ -137,11 +138,18 @@ def load() -> ctypes.CDLL:
     L.fpt_normals_fill.argtypes = [i32, u64, u64, u64, u64, vp, vp]
     L.fpt_version.restype = ctypes.c_char_p
     L.fpt_engine_occupancy.argtypes = [i32, i32, P(ctypes.c_int32)]
+    pd = P(f64)
+    L.fpt_from_paper_units.argtypes = [f64] * 5 + [pd] * 4
+    L.fpt_to_paper_units.argtypes = [f64] * 5 + [pd] * 4
+    L.fpt_junction_paper_units.argtypes = [f64] * 4 + [pd] * 4
+    L.fpt_sweep_delta_gamma.argtypes = [f64] * 4 + [pd]
     for name in ("fpt_plain_launch", "fpt_reduce_steps", "fpt_sums_finish", "fpt_create",
                  "fpt_submit", "fpt_step", "fpt_poll", "fpt_wait", "fpt_histogram",
                  "fpt_per_traj", "fpt_per_traj_steps", "fpt_release", "fpt_get_counters",
                  "fpt_destroy", "fpt_philox_fill", "fpt_normals_fill", "fpt_request_sums",
-                 "fpt_run_noalloc", "fpt_checkpoint", "fpt_restore", "fpt_engine_occupancy"):
+                 "fpt_run_noalloc", "fpt_checkpoint", "fpt_restore", "fpt_engine_occupancy",
+                 "fpt_from_paper_units", "fpt_to_paper_units", "fpt_junction_paper_units",
+                 "fpt_sweep_delta_gamma"):
         getattr(L, name).restype = ctypes.c_int
     _lib = L
     return L

@@ -183,3 +183,87 @@ extern "C" const char *fpt_status_string(fpt_status s) {
 }
 
 extern "C" const char *fpt_version(void) { return "fpt-gb300 0.1 (sm_103a)"; }
+
+// ---- paper units (Sec. II.A, Eq. JJn) <-> engine units ----------------------------------------
+// The paper's time unit is hbar / E_C; rescaling time by sqrt(V0) (V0 = E_J / E_C) gives the
+// plasma-frequency units of the engine.  Arithmetic in IEEE double, contraction off.
+
+static bool positive_finite(double x) { return std::isfinite(x) && x > 0; }
+
+extern "C" fpt_status fpt_from_paper_units(double V0, double beta, double theta, double h,
+                                           double delta_gamma, double *alpha, double *D,
+                                           double *dt, double *nu) {
+    if (!alpha || !D || !dt || !nu) {
+        set_error("NULL output");
+        return FPT_EINVAL;
+    }
+    if (!positive_finite(V0) || !positive_finite(h) || !std::isfinite(beta) || !std::isfinite(theta) ||
+        !std::isfinite(delta_gamma)) {
+        set_error("V0 and h must be positive; beta, theta, delta_gamma finite");
+        return FPT_EINVAL;
+    }
+    const double s = std::sqrt(V0);
+    *dt = s * h;
+    *alpha = beta / s;
+    *D = theta / V0;
+    *nu = delta_gamma / *dt;
+    return FPT_OK;
+}
+
+extern "C" fpt_status fpt_to_paper_units(double alpha, double D, double dt, double nu, double V0,
+                                         double *beta, double *theta, double *h,
+                                         double *delta_gamma) {
+    if (!beta || !theta || !h || !delta_gamma) {
+        set_error("NULL output");
+        return FPT_EINVAL;
+    }
+    if (!positive_finite(V0) || !positive_finite(dt) || !std::isfinite(alpha) || !std::isfinite(D) ||
+        !std::isfinite(nu)) {
+        set_error("V0 and dt must be positive; alpha, D, nu finite");
+        return FPT_EINVAL;
+    }
+    const double s = std::sqrt(V0);
+    *h = dt / s;
+    *beta = alpha * s;
+    *theta = D * V0;
+    *delta_gamma = nu * dt;
+    return FPT_OK;
+}
+
+extern "C" fpt_status fpt_junction_paper_units(double R, double C, double Ic, double T, double *V0,
+                                               double *beta, double *theta, double *time_unit_s) {
+    if (!V0 || !beta || !theta || !time_unit_s) {
+        set_error("NULL output");
+        return FPT_EINVAL;
+    }
+    if (!positive_finite(R) || !positive_finite(C) || !positive_finite(Ic) || !(T >= 0) ||
+        !std::isfinite(T)) {
+        set_error("R, C, Ic must be positive and T >= 0");
+        return FPT_EINVAL;
+    }
+    const double hbar = 1.054571817e-34, e_charge = 1.602176634e-19, k_b = 1.380649e-23;   // SI
+    const double two_e = 2.0 * e_charge;
+    const double e_j = hbar * Ic / two_e;        // Josephson energy
+    const double e_c = two_e * two_e / C;        // charging energy of a Cooper pair
+    *V0 = e_j / e_c;
+    *beta = hbar / (R * two_e * two_e);
+    *theta = k_b * T / e_c;
+    *time_unit_s = hbar / e_c;
+    return FPT_OK;
+}
+
+extern "C" fpt_status fpt_sweep_delta_gamma(double sweep_hz, double h, double time_unit_s, double span,
+                                            double *delta_gamma) {
+    if (!delta_gamma) {
+        set_error("NULL output");
+        return FPT_EINVAL;
+    }
+    if (!positive_finite(sweep_hz) || !positive_finite(h) || !positive_finite(time_unit_s) ||
+        !std::isfinite(span)) {
+        set_error("sweep_hz, h and time_unit_s must be positive, span finite");
+        return FPT_EINVAL;
+    }
+    const double ramp_time_s = 0.5 / sweep_hz;   // half a period of a triangular sweep
+    *delta_gamma = span / (ramp_time_s / (h * time_unit_s));
+    return FPT_OK;
+}
