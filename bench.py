@@ -537,6 +537,28 @@ def run_ours(args):
         fp64 = fp64_equal_accuracy(pkg, torch, local, pts[11], args.block, args.traj_per_thread,
                                    args.blocks_per_sm)
 
+    # the same sweep in 4096-step launches, driven through one fpt_step call of many iterations
+    # (the host loop keeps the next launch queued): wall-clock rate against the long launches
+    short_launches = None
+    if rank == 0:
+        with pkg.Engine(local, chunk_steps=4096, traj_per_thread=args.traj_per_thread,
+                        threads_per_block=args.block, blocks_per_sm=args.blocks_per_sm) as e6:
+            for d in pts:
+                e6.submit(pkg.params_from(d), n_traj, d["seed"])
+            e6.step(4)
+            s0 = e6.counters()
+            t6 = time.perf_counter()
+            e6.step(100)
+            w6 = time.perf_counter() - t6
+            s1 = e6.counters()
+        st6 = s1["useful_steps"] - s0["useful_steps"]
+        short_launches = {"chunk_steps": 4096, "iterations": 100,
+                          "value": st6 / w6, "unit": UNIT,
+                          "kernel_gstep_s": st6 / ((s1["kernel_ms"] - s0["kernel_ms"]) / 1e3) / 1e9,
+                          "kernel_share_of_wall": (s1["kernel_ms"] - s0["kernel_ms"]) / 1e3 / w6,
+                          "workload": "the same sweep, 4096-step launches, one fpt_step(100) "
+                                      "call, wall clock"}
+
     # the same sweep with the stochastic Heun integrator (4 XU evaluations per step: two sin of
     # the predictor-corrector, half of the Box-Muller pair), a few engine iterations
     heun = None
@@ -706,6 +728,7 @@ def run_ours(args):
         "e2e": e2e,
         "fp64_equal_accuracy": fp64,
         "heun": heun,
+        "short_launches": short_launches,
         "other_workloads": mix,
         "autotune": None if not tuned else {
             "best": tuned["best"], "chunk_for_2pct_overhead": tuned["chunk_steps"],
