@@ -430,10 +430,19 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
                                unsigned &cursor, unsigned long long &useful, unsigned &n_esc,
                                unsigned &n_cens) {
     const unsigned nb = E.chunk_blocks;
+    // Steps are counted when the number of active lanes changes (at events) and at the end:
+    // useful += kBlockSteps x active lanes x blocks since the last count.
+    unsigned b_count = b;
+    // Constant bias (R = 0): the bias line is the same in every block until an event changes the
+    // lane (re-base, refill); it is formed here and after each event.
+    float gs[T], gsl[T];
+#pragma unroll
+    for (int t = 0; t < T; ++t)
+        if constexpr (!R) bias_line(fmaf(L[t].nudt, L[t].Jf, L[t].gb), L[t].nudt, L[t].dt, gs[t], gsl[t]);
     while (b < nb) {
         // the block's normals: Philox blocks c .. c + kBlockPhilox - 1 (c is a multiple of
         // kBlockPhilox, so c_lo + h never carries into c_hi)
-        float rr[T][2 * kBlockPhilox], tg[T][kBlockSteps], gs[T], gsl[T];
+        float rr[T][2 * kBlockPhilox], tg[T][kBlockSteps];
 #pragma unroll
         for (int t = 0; t < T; ++t) {
 #pragma unroll
@@ -442,7 +451,7 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
                 bm_pair_f32(x.x, x.y, L[t].bmc, rr[t][2 * h], tg[t][4 * h], tg[t][4 * h + 1]);
                 bm_pair_f32(x.z, x.w, L[t].bmc, rr[t][2 * h + 1], tg[t][4 * h + 2], tg[t][4 * h + 3]);
             }
-            bias_line(fmaf(L[t].nudt, L[t].Jf, L[t].gb), L[t].nudt, L[t].dt, gs[t], gsl[t]);
+            if constexpr (R) bias_line(fmaf(L[t].nudt, L[t].Jf, L[t].gb), L[t].nudt, L[t].dt, gs[t], gsl[t]);
         }
         // The block's steps without a branch: each lane only tracks the largest phase of the block.
         // In the rare block where it reached the lane's bound hb, the lane's block is replayed
@@ -464,12 +473,11 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
                 mx[t] = fmaxf(mx[t], L[t].r);
             }
         }
-        useful += static_cast<unsigned long long>(kBlockSteps) * static_cast<unsigned>(n_active);
         bool ev = false;
 #pragma unroll
         for (int t = 0; t < T; ++t) {
             L[t].c_lo += kBlockPhilox;
-            L[t].Jf += static_cast<float>(kBlockSteps);
+            if constexpr (R) L[t].Jf += static_cast<float>(kBlockSteps);
             L[t].budget -= 1u;
             // one vote covers every rare case: a bound reached (escape or upper wrap), the
             // countdown (step budget, bias re-base, low-word carry) and the lower wrap
@@ -477,6 +485,8 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
         }
         ++b;
         if (__any_sync(kFull, ev)) {
+            useful += static_cast<unsigned long long>(kBlockSteps) * static_cast<unsigned>(n_active) * (b - b_count);
+            b_count = b;
 #pragma unroll
             for (int t = 0; t < T; ++t) {
                 if (mx[t] >= L[t].hb) {
@@ -499,8 +509,14 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
             finish_lanes(L, E, V, useful, n_active, n_esc, n_cens);
             refill(L, E, V, kind_of(M, H, R), n_active, cursor);
             if (!__any_sync(kFull, n_active > 0)) break;
+            if constexpr (!R) {
+#pragma unroll
+                for (int t = 0; t < T; ++t)
+                    bias_line(fmaf(L[t].nudt, L[t].Jf, L[t].gb), L[t].nudt, L[t].dt, gs[t], gsl[t]);
+            }
         }
     }
+    useful += static_cast<unsigned long long>(kBlockSteps) * static_cast<unsigned>(n_active) * (b - b_count);
     return b;
 }
 
