@@ -31,6 +31,8 @@
 #include <thread>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "engine_dev.h"
 #include "internal.h"
 
@@ -43,6 +45,18 @@ cudaError_t engine_chunk_occupancy(int T, int block, int *blocks_per_sm);
 
 using namespace fpt;
 using Clock = std::chrono::steady_clock;
+
+namespace {
+// NVTX range around a scope (header-only NVTX: a no-op unless a profiler is attached), so a
+// timeline shows the host side of each engine iteration: admission and lists, enqueue, waiting
+// for a launch and processing its status.
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+}  // namespace
 
 namespace {
 
@@ -491,6 +505,7 @@ void process_status(fpt_engine *e) {
 // Wait for the oldest enqueued iteration and take its status: stable copies for fpt_poll,
 // admission and list building, finished requests, freed slots, counters and kernel time.
 fpt_status complete_oldest(fpt_engine *e) {
+    NvtxRange range("fpt: wait and process status");
     IterIO &B = e->iters[e->flight[0]];
     CK(cudaEventSynchronize(B.done));
     float ms = 0.0f;
@@ -521,12 +536,14 @@ fpt_status iteration(fpt_engine *e) {
     }
     IterIO &B = e->iters[e->next_io];
     {
+        NvtxRange range("fpt: admission and lists");
         std::lock_guard<std::mutex> lk(e->mu);
         fpt_status st = admit(e);
         if (st != FPT_OK) return st;
         build_lists(e, B);
     }
     B.seq = e->enq_seq++;
+    NvtxRange range("fpt: enqueue iteration");
     fpt_status st = enqueue_iteration(e, B);
     if (st != FPT_OK) return st;
     CK(cudaEventRecord(B.done, e->stream));
