@@ -79,6 +79,10 @@ def parse():
     ap.add_argument("--no-autotune", action="store_true",
                     help="use --traj-per-thread / --block as given instead of the autotuner's choice")
     ap.add_argument("--serving-requests", type=int, default=60)
+    ap.add_argument("--precision-report", action="store_true",
+                    help="instead of the benchmark: the FP32 engine against the FP64 kernel on "
+                         "the same ids for the ramp sweep and uneven-batch sets, one JSON line "
+                         "per case (several minutes)")
     return ap.parse_args()
 
 
@@ -749,8 +753,30 @@ def run_ours(args):
         pg.destroy_process_group()
 
 
+def precision_report(device: int = 0):
+    """The FP32-vs-FP64 table of every config: the ramp sweep at nu = 1e-5 and 1e-6 (4096 paired
+    trajectories each) and uneven-batch sets spanning 10^3 .. 10^8 steps."""
+    import workloads
+    from paper_1802_05065_gb300 import build as _b
+    from paper_1802_05065_gb300 import precision
+    _b.build()
+    cases = [(f"ramp nu={d['nu']:g}", d, 4096) for d in workloads.ramp_sweep(n_traj=4096)[:2]]
+    for p, n in (workloads.precision_uneven_cases(8, 1e3, 3e5) +
+                 workloads.precision_uneven_cases(3, 1e6, 2e8)):
+        kind = "ramped" if p["nu"] else "constant"
+        cases.append((f"uneven {kind} est_length={p['est_length']:.3g}", p, n))
+    for name, d, n in cases:
+        row = {"case": name, "model": d["model"], "output": d["output"], "alpha": d["alpha"],
+               "D": d["D"], "gamma0": d["gamma0"], "nu": d["nu"], "dt": d["dt"]}
+        row.update(precision.paired(d, n, int(d["seed"]), device))
+        print(json.dumps(row), flush=True)
+
+
 def main():
     args = parse()
+    if args.precision_report:
+        precision_report()
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -10,14 +10,11 @@ two-sample Kolmogorov-Smirnov p-value of the two result distributions.
 
 Cost: the FP64 kernel advances one trajectory per thread at ~3e5 steps/s on a GB300, so a case
 takes (trajectory length / 3e5) seconds whatever its trajectory count up to a few thousand.
-
-    python -m paper_1802_05065_gb300.precision            # the full report (several minutes)
+The report over every config is `python bench.py --precision-report`.
 """
 from __future__ import annotations
 
-import json
 import math
-import sys
 
 import numpy as np
 
@@ -55,40 +52,3 @@ def paired(d: dict, n: int, seed: int, device: int = 0, chunk_steps: int = 65536
         "relative_paired_diff": float(np.mean(diff) / r64.mean) if diff.size and r64.mean else float("nan"),
         "ks_p": float(sst.ks_2samp(x32[k32 >= 0], x64[k64 >= 0]).pvalue),
     }
-
-
-def uneven_cases(n_cases: int = 8, min_length: float = 1e3, max_length: float = 3e5,
-                 fp64_steps: float = 2e10, max_n: int = 4096) -> list:
-    """n_cases sets of the uneven batch whose estimated mean lengths span min_length ..
-    max_length steps (evenly spaced picks in the sorted list), with
-    n = min(set size, max_n, fp64_steps / length) trajectories."""
-    import workloads
-    sets = sorted((p for p in workloads.uneven_batch()
-                   if min_length <= p["est_length"] <= max_length), key=lambda p: p["est_length"])
-    idx = np.unique(np.round(np.linspace(0, len(sets) - 1, n_cases)).astype(int))
-    out = []
-    for i in idx:
-        p = sets[int(i)]
-        n = int(max(64, min(p["n_traj"], max_n, fp64_steps / p["est_length"])))
-        out.append((p, n))
-    return out
-
-
-def report(device: int = 0):
-    """Every case of the precision table: the ramp sweep at nu = 1e-5 and 1e-6 (4096 paired
-    trajectories each) and uneven-batch sets spanning 10^3 .. 10^8 steps."""
-    import workloads
-    ramps = workloads.ramp_sweep(n_traj=4096)
-    cases = [(f"ramp nu={d['nu']:g}", d, 4096) for d in ramps[:2]]
-    for p, n in uneven_cases(8, 1e3, 3e5) + uneven_cases(3, 1e6, 2e8):
-        kind = "ramped" if p["nu"] else "constant"
-        cases.append((f"uneven {kind} est_length={p['est_length']:.3g}", p, n))
-    for name, d, n in cases:
-        row = {"case": name, "model": d["model"], "output": d["output"], "alpha": d["alpha"],
-               "D": d["D"], "gamma0": d["gamma0"], "nu": d["nu"], "dt": d["dt"]}
-        row.update(paired(d, n, int(d["seed"]), device))
-        print(json.dumps(row), flush=True)
-
-
-if __name__ == "__main__":
-    report(int(sys.argv[1]) if len(sys.argv) > 1 else 0)

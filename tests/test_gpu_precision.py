@@ -9,8 +9,8 @@ the error single precision adds to a result -- must stay within 3 of its own sta
 few 1e-6 of the result in most cases.  In weakly damped sets the FP32 and FP64 trajectories of one
 id decorrelate after many oscillations, and the paired difference becomes statistical.)  The full
 table (nu = 1e-6 and uneven sets up to 10^8 steps) comes from
-`python -m paper_1802_05065_gb300.precision`; these cases are the ones the FP64 kernel finishes
-in seconds (it advances one trajectory per thread at ~3e5 steps/s).
+`python bench.py --precision-report`; these cases are the ones the FP64 kernel finishes in
+seconds (it advances one trajectory per thread at ~3e5 steps/s).
 """
 import pytest
 
@@ -40,7 +40,7 @@ def test_uneven_batch_sets_fp32_vs_fp64():
     """Eight sets of the uneven batch with estimated mean lengths from 10^3 to 3 x 10^5 steps
     (constant and ramped bias, alpha 0.01..1, D 1e-3..0.1)."""
     from paper_1802_05065_gb300 import precision
-    cases = precision.uneven_cases(8, 1e3, 3e5)
+    cases = workloads.precision_uneven_cases(8, 1e3, 3e5)
     assert len(cases) == 8
     lengths = sorted(p["est_length"] for p, _ in cases)
     assert lengths[0] < 3e3 and lengths[-1] > 1e5

@@ -127,6 +127,20 @@ def uneven_batch(n_sets: int = 256, seed: int = 0, log2_traj=(12, 18),
     return out
 
 
+def precision_uneven_cases(n_cases: int = 8, min_length: float = 1e3, max_length: float = 3e5,
+                           fp64_steps: float = 2e10, max_n: int = 4096) -> list:
+    """Sets of the uneven batch for the FP32-vs-FP64 comparison: n_cases sets whose estimated
+    mean lengths lie in [min_length, max_length] steps, picked evenly along the sorted list, each
+    with n = min(set size, max_n, fp64_steps / length) trajectories (so the FP64 side stays
+    within ~fp64_steps steps).  Returns a list of (params, n)."""
+    sets = sorted((p for p in uneven_batch() if min_length <= p["est_length"] <= max_length),
+                  key=lambda p: p["est_length"])
+    idx = np.unique(np.round(np.linspace(0, len(sets) - 1, n_cases)).astype(int))
+    return [(sets[int(i)], int(max(64, min(sets[int(i)]["n_traj"], max_n,
+                                               fp64_steps / sets[int(i)]["est_length"]))))
+            for i in idx]
+
+
 def serving_stream(n_requests: int = 200, rate_hz: float = 200.0, seed: int = 0,
                    log2_traj=(12, 20), stop_rse: float = 0.01) -> list:
     """Poisson arrivals (mean rate_hz) of requests drawn as in the uneven batch, each with
