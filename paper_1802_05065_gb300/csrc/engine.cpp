@@ -102,9 +102,11 @@ struct CkptHeader {
 constexpr uint64_t kCkptMagic = 0x5450464B43505446ull;   // "FTPCKFPT"
 constexpr uint64_t kCkptVersion = 3;   // 3: id-block sums as 32-bit limbs, histogram rows per hist_rows
 
-// Ring of suspended trajectories: never more than the lanes can hold twice over.
+// Ring of suspended trajectories: twice the lanes (suspensions) plus every warp's reservoir of
+// unstarted ids returned at a launch end, and never more than the request's trajectories.
 uint32_t park_capacity(uint64_t n_traj, unsigned lanes) {
-    const uint64_t cap = std::min<uint64_t>(n_traj, 2ull * lanes);
+    const uint64_t warps = (lanes + 31) / 32;
+    const uint64_t cap = std::min<uint64_t>(n_traj, 2ull * lanes + static_cast<uint64_t>(kReserveIds) * warps);
     return static_cast<uint32_t>(std::max<uint64_t>(cap, 1));
 }
 

@@ -25,6 +25,12 @@ constexpr int kNumKinds = 8;
 // Resident request slots an engine may have (the kernel keeps a per-slot view in shared memory).
 constexpr int kMaxRequests = 1024;
 
+// New trajectory ids a warp may hold beyond what its idle lanes need when it claims from a queue
+// head (its reservoir, used by its next refills without an atomic).  Leftovers go back into the
+// request's ring of suspended trajectories at the end of a launch, which therefore has room for
+// kReserveIds per warp on top of twice the lanes.
+constexpr int kReserveIds = 32;
+
 // Philox blocks (of 4 steps) between re-bases of a trajectory's single-precision bias: gamma_k is
 // formed as gs + nu dt (s + 1) with gs = gb + nu dt Jf and gb = gamma0 + nu dt 4 c_base in FP64,
 // c_base the trajectory's own block count rounded down to a multiple of kRebaseBlocks, so the

@@ -174,10 +174,17 @@ __device__ __forceinline__ int hist_bin(const SlotDev *S, unsigned long long k) 
 //   ok[s]   bit 0: request s has ids left to claim, bit 1: it has suspended trajectories to
 //           resume (both as of the launch start; cleared when a warp finds them exhausted),
 //   held[s] lanes of this CTA that hold a trajectory of s (the CTA's share of the fair-share
-//           cap is checked against it, so claims need no global read).
+//           cap is checked against it, so claims need no global read),
+//   budget[s] reservoir ids this CTA may hold for s: its share of the room the request's ring
+//           had at launch start beyond one slot per lane (kept for suspensions), so that the
+//           reservoirs returned to the ring at the end of the launch always fit.
 struct CtaView {
     unsigned *ok;
     int *held;
+    int *budget;                 // ids this CTA's warps may still hold in reservoirs, per request
+    int *res_slot, *res_cnt;     // per warp of the CTA: reservoir request and count ...
+    unsigned long long *res_base;   // ... and first id (ids res_base .. res_base + res_cnt - 1)
+    int *started;                // per warp: trajectories it started in this launch
 };
 
 // Publish the trajectories finishing in this warp at this block end (warp-collective: every lane
@@ -324,15 +331,17 @@ __device__ __forceinline__ void finish_lanes(Lane (&L)[T], const EngineDev &E, c
 }
 
 // Warp-collective refill of idle lanes with trajectories of requests of kind `kind`.  Lane 0
-// takes, per request in round-robin order, suspended trajectories first and then new ids from
-// the request's queue head: one atomic addition on the head per claim, and the in-flight count
-// raised by what was actually obtained (an addition nobody waits for).  While some request is
+// takes, per request in round-robin order, suspended trajectories first, then ids from the
+// warp's reservoir, then new ids from the request's queue head: one atomic addition on the head
+// per claim, claiming up to kReserveIds more for the reservoir when it is empty and the CTA's
+// budget allows, and the in-flight count raised by what was actually started (an addition
+// nobody waits for).  While some request is
 // starved (strict caps, set by the host with preemption orders) each request is kept within
 // this CTA's share of its fair-share cap, counted in shared memory; otherwise lanes take work
 // from the first request that has some, so no lane idles while any request has work.
 template <int T>
 __device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, const CtaView &V, int kind,
-                                       int &n_active, unsigned &cursor) {
+                                       int &n_active, unsigned &cursor, unsigned b) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     unsigned idle[T];
@@ -349,15 +358,20 @@ __device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, const C
     if (cnt <= 0) return;
     const int *list = E.act_list + kind * E.max_requests;
     const bool capped = *E.strict != 0;
+    const int wl = static_cast<int>(threadIdx.x >> 5);
+    // A warp that holds a reservoir serves its request first, so the reservoir drains.
+    __syncwarp();
+    const int rs = V.res_slot[wl];
+    const bool res_first = V.res_cnt[wl] > 0 && rs >= 0 && rs < E.max_requests && E.slots[rs].kind == kind;
     {
-        for (int scanned = 0; scanned < cnt && total > 0; ++scanned) {
-            const int s = list[cursor % static_cast<unsigned>(cnt)];
-            ++cursor;
+        for (int scanned = res_first ? -1 : 0; scanned < cnt && total > 0; ++scanned) {
+            const int s = scanned < 0 ? rs : list[cursor % static_cast<unsigned>(cnt)];
+            if (scanned >= 0) ++cursor;
             if (!checked(E, s >= 0 && s < E.max_requests, kChkSlot)) continue;
-            unsigned long long base = 0;
-            int got = 0, gp = 0;
+            unsigned long long base = 0, rb = 0;
+            int got = 0, gp = 0, rt = 0;
             unsigned p0 = 0;
-            if (lane == 0 && (V.ok[s] & 3u)) {
+            if (lane == 0 && ((V.ok[s] & 3u) || V.res_slot[wl] == s)) {
                 SlotCtl *C = E.ctl + s;
                 const unsigned long long n_traj = E.slots[s].n_traj;
                 int want = total;
@@ -366,6 +380,7 @@ __device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, const C
                     const int room = cap - V.held[s];
                     want = room < 0 ? 0 : (room < want ? room : want);
                 }
+                // 1. suspended trajectories
                 if (want > 0 && (V.ok[s] & 2u)) {
                     const int pv = atomicSub(&C->park_avail, want);
                     if (pv <= 0) {
@@ -379,24 +394,63 @@ __device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, const C
                     }
                 }
                 got = gp;
-                if (want > gp && (V.ok[s] & 1u)) {
-                    const int wn = want - gp;
-                    base = atomicAdd(&C->head, static_cast<unsigned long long>(wn));
+                // 2. this warp's reservoir of ids claimed earlier
+                if (want > got && V.res_slot[wl] == s && V.res_cnt[wl] > 0) {
+                    rt = want - got < V.res_cnt[wl] ? want - got : V.res_cnt[wl];
+                    rb = V.res_base[wl];
+                    V.res_base[wl] += static_cast<unsigned long long>(rt);
+                    V.res_cnt[wl] -= rt;
+                    atomicAdd(&V.budget[s], rt);
+                    got += rt;
+                }
+                // 3. the queue head, with more for the reservoir when it is free: as many as this
+                //    warp is expected to start in the rest of the launch at its rate so far (at
+                //    most kReserveIds, none while caps are enforced), within the CTA's budget.
+                //    Only warps that start a trajectory at least every 8 blocks keep one: for
+                //    long trajectories the ids would mostly return to the ring unused.
+                if (want > got && (V.ok[s] & 1u)) {
+                    const int wn = want - got;
+                    int extra = 0;
+                    if (V.res_cnt[wl] == 0 && !capped && b > 0 && 8u * static_cast<unsigned>(V.started[wl]) >= b) {
+                        const unsigned long long expect =
+                            static_cast<unsigned long long>(V.started[wl]) * (E.chunk_blocks - b) / b;
+                        const int want_extra = expect < static_cast<unsigned long long>(kReserveIds)
+                                                   ? static_cast<int>(expect) : kReserveIds;
+                        if (want_extra > 0) {
+                            if (atomicSub(&V.budget[s], want_extra) >= want_extra) extra = want_extra;
+                            else atomicAdd(&V.budget[s], want_extra);
+                        }
+                    }
+                    const int cl = wn + extra;
+                    base = atomicAdd(&C->head, static_cast<unsigned long long>(cl));
+                    int keep = 0;
                     if (base < n_traj) {
                         const unsigned long long left = n_traj - base;
-                        got += left < static_cast<unsigned long long>(wn) ? static_cast<int>(left) : wn;
+                        const int avail = left < static_cast<unsigned long long>(cl) ? static_cast<int>(left) : cl;
+                        const int use = avail < wn ? avail : wn;
+                        got += use;
+                        keep = avail - use;
+                        if (keep > 0) {
+                            V.res_slot[wl] = s;
+                            V.res_base[wl] = base + static_cast<unsigned long long>(use);
+                            V.res_cnt[wl] = keep;
+                        }
                     }
-                    if (base + static_cast<unsigned long long>(wn) >= n_traj) atomicAnd(&V.ok[s], ~1u);
+                    if (extra > keep) atomicAdd(&V.budget[s], extra - keep);
+                    if (base + static_cast<unsigned long long>(cl) >= n_traj) atomicAnd(&V.ok[s], ~1u);
                 }
                 if (got) {
                     atomicAdd(&C->inflight, got);
                     atomicAdd(&V.held[s], got);
+                    V.started[wl] += got;
                 }
             }
             got = __shfl_sync(kFull, got, 0);
             if (got == 0) continue;
             gp = __shfl_sync(kFull, gp, 0);
             p0 = __shfl_sync(kFull, p0, 0);
+            rt = __shfl_sync(kFull, rt, 0);
+            rb = __shfl_sync(kFull, rb, 0);
             base = __shfl_sync(kFull, base, 0);
             const SlotDev *S = E.slots + s;
             int before = 0;
@@ -408,9 +462,11 @@ __device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, const C
                     if (rank < gp) {
                         const unsigned pi = (p0 + static_cast<unsigned>(rank)) % S->park_cap;
                         if (checked(E, pi < S->park_cap, kChkPark)) resume_lane(L[t], E, s, S->park[pi]);
+                    } else if (rank < gp + rt) {
+                        init_lane(L[t], E, s, rb + static_cast<unsigned long long>(rank - gp));
+                    } else {
+                        init_lane(L[t], E, s, base + static_cast<unsigned long long>(rank - gp - rt));
                     }
-                    else
-                        init_lane(L[t], E, s, base + static_cast<unsigned long long>(rank - gp));
                     ++n_active;
                 }
                 before += __popc(m);
@@ -507,7 +563,7 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
                 }
             }
             finish_lanes(L, E, V, useful, n_active, n_esc, n_cens);
-            refill(L, E, V, kind_of(M, H, R), n_active, cursor);
+            refill(L, E, V, kind_of(M, H, R), n_active, cursor, b);
             if (!__any_sync(kFull, n_active > 0)) break;
             if constexpr (!R) {
 #pragma unroll
@@ -532,11 +588,20 @@ __global__ void __launch_bounds__(T == 1 ? 640 : 256, 1) engine_chunk_kernel(Eng
     // This CTA's view of the requests for the launch: which listed requests have ids or suspended
     // trajectories to hand out, and how many of its lanes hold each.
     __shared__ unsigned sh_ok[kMaxRequests];
-    __shared__ int sh_held[kMaxRequests];
-    const CtaView V{sh_ok, sh_held};
+    __shared__ int sh_held[kMaxRequests], sh_budget[kMaxRequests];
+    __shared__ int sh_res_slot[32], sh_res_cnt[32], sh_started[32];   // a CTA has at most 32 warps
+    __shared__ unsigned long long sh_res_base[32];
+    const CtaView V{sh_ok, sh_held, sh_budget, sh_res_slot, sh_res_cnt, sh_res_base, sh_started};
     for (int s = threadIdx.x; s < E.max_requests; s += blockDim.x) {
         sh_ok[s] = 0u;
         sh_held[s] = 0;
+        sh_budget[s] = 0;
+    }
+    if (threadIdx.x < 32) {
+        sh_res_slot[threadIdx.x] = -1;
+        sh_res_cnt[threadIdx.x] = 0;
+        sh_res_base[threadIdx.x] = 0ull;
+        sh_started[threadIdx.x] = 0;
     }
     __syncthreads();
     {
@@ -549,6 +614,11 @@ __global__ void __launch_bounds__(T == 1 ? 640 : 256, 1) engine_chunk_kernel(Eng
             const SlotCtl &C = E.ctl[s];
             if (vload(C.state) != kSlotActive) continue;
             sh_ok[s] = (vload(C.head) < E.slots[s].n_traj ? 1u : 0u) | (vload(C.park_avail) > 0 ? 2u : 0u);
+            // reservoir room: what the ring can still take beyond one entry per lane (the most
+            // suspensions of this launch could add), shared equally by the CTAs
+            const long long room = static_cast<long long>(E.slots[s].park_cap) - vload(C.park_used) -
+                                   static_cast<long long>(E.n_lanes);
+            sh_budget[s] = room > 0 ? static_cast<int>(room / gridDim.x) : 0;
         }
     }
     Lane L[T];
@@ -589,7 +659,7 @@ __global__ void __launch_bounds__(T == 1 ? 640 : 256, 1) engine_chunk_kernel(Eng
     unsigned cursor = E.warp_cursor[warp];
     unsigned long long useful = 0;
     unsigned n_esc = 0, n_cens = 0;
-    if (kind >= 0) refill(L, E, V, kind, n_active, cursor);
+    if (kind >= 0) refill(L, E, V, kind, n_active, cursor, 0u);
     unsigned b = 0;
     while (b < E.chunk_blocks) {
         if (kind < 0) {
@@ -597,7 +667,7 @@ __global__ void __launch_bounds__(T == 1 ? 640 : 256, 1) engine_chunk_kernel(Eng
             const int first = static_cast<int>(warp % kNumKinds);
             for (int q = 0; q < kNumKinds && kind < 0; ++q) {
                 const int m = (first + q) % kNumKinds;
-                refill(L, E, V, m, n_active, cursor);
+                refill(L, E, V, m, n_active, cursor, b);
                 if (__any_sync(kFull, n_active > 0)) kind = m;
             }
             if (kind < 0) break;
@@ -657,6 +727,33 @@ __global__ void __launch_bounds__(T == 1 ? 640 : 256, 1) engine_chunk_kernel(Eng
         atomicSub(&C->inflight, 1);
         L[t].slot = -1;
         --n_active;
+    }
+    // Ids left in this warp's reservoir go back to their request as suspended trajectories that
+    // have not started (state r0, v0, w0 at step 0: resuming one is starting it).  The CTA's
+    // budget kept the ring's room for them.
+    {
+        __syncwarp();
+        const int wl = static_cast<int>(threadIdx.x >> 5);
+        const int rs = sh_res_slot[wl], rc = sh_res_cnt[wl];
+        if (rs >= 0 && rc > 0 && checked(E, rs < E.max_requests, kChkSlot)) {
+            SlotCtl *C = E.ctl + rs;
+            const SlotDev *S = E.slots + rs;
+            for (int j = lane; j < rc; j += 32) {
+                const unsigned long long gid = S->traj_offset + sh_res_base[wl] + static_cast<unsigned long long>(j);
+                const int used = atomicAdd(&C->park_used, 1);
+                checked(E, used < static_cast<int>(S->park_cap), kChkPark);   // the budget's invariant
+                const unsigned pi = atomicAdd(&C->park_tail, 1u);
+                if (!checked(E, pi % S->park_cap < S->park_cap, kChkPark)) continue;
+                ParkEntry &P = S->park[pi % S->park_cap];
+                P.r = S->r0;
+                P.v = S->v0;
+                P.w = S->w0;
+                P.c_lo = P.c_hi = 0u;
+                P.gid_lo = static_cast<unsigned>(gid);
+                P.gid_hi = static_cast<unsigned>(gid >> 32);
+                P.pad = 0;
+            }
+        }
     }
     if (!__any_sync(kFull, n_active > 0)) kind = -1;
 #pragma unroll
