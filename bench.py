@@ -251,10 +251,10 @@ def run_reference(args):
 # (ncu capture summarised in profiles/engine_chunk_kernel__overdamped_sweep.md): the lane state is
 # read and written once per launch, whatever the number of steps, so a 65 536-step launch moves
 # the same bytes as the captured 4096-step one.
-TRAFFIC_BYTES_PER_LAUNCH = 3.63e6
+TRAFFIC_BYTES_PER_LAUNCH = 3.64e6
 # warp instructions x 32 / lane-steps of the same capture (smsp__inst_executed): the issue bound
 # of the current kernel is 4 schedulers x 32 lanes x N_SM x f / this
-INSTRUCTIONS_PER_STEP = 22.71
+INSTRUCTIONS_PER_STEP = 22.39
 
 
 def roofline_model(n_sm: int, f_mhz: float):
