@@ -501,11 +501,15 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
         float rr[T][2 * kBlockPhilox], tg[T][kBlockSteps];
 #pragma unroll
         for (int t = 0; t < T; ++t) {
+            // the block's Philox words first, then their Box-Muller pairs (measured +0.4 % over
+            // interleaving them per call: the MUFU work of the pairs comes in one stretch)
+            uint4 xs[kBlockPhilox];
+#pragma unroll
+            for (int h = 0; h < kBlockPhilox; ++h) xs[h] = philox_lane_block(L[t].P, L[t].c_lo, static_cast<unsigned>(h));
 #pragma unroll
             for (int h = 0; h < kBlockPhilox; ++h) {
-                const uint4 x = philox_lane_block(L[t].P, L[t].c_lo, static_cast<unsigned>(h));
-                bm_pair_f32(x.x, x.y, L[t].bmc, rr[t][2 * h], tg[t][4 * h], tg[t][4 * h + 1]);
-                bm_pair_f32(x.z, x.w, L[t].bmc, rr[t][2 * h + 1], tg[t][4 * h + 2], tg[t][4 * h + 3]);
+                bm_pair_f32(xs[h].x, xs[h].y, L[t].bmc, rr[t][2 * h], tg[t][4 * h], tg[t][4 * h + 1]);
+                bm_pair_f32(xs[h].z, xs[h].w, L[t].bmc, rr[t][2 * h + 1], tg[t][4 * h + 2], tg[t][4 * h + 3]);
             }
             if constexpr (R) bias_line(fmaf(L[t].nudt, L[t].Jf, L[t].gb), L[t].nudt, L[t].dt, gs[t], gsl[t]);
         }
