@@ -40,7 +40,9 @@ with m.Engine(0, chunk_steps=4096) as eng:
     ids[0] = eng.restore(blob)
     for rid, (d, n, s) in zip(ids, reqs):
         r = eng.wait(rid, 600.0)
-        st = eng.per_traj_steps(rid, n)
+        # the result's trajectories: ids past n_used (integrated before a stop rule ended the
+        # request) depend on scheduling and are not part of it
+        st = eng.per_traj_steps(rid, n)[: r.n_used]
         h, u, o = eng.histogram(rid, d["hist_bins"])
         out["results"].append([r.n_used, r.n_escaped, r.n_censored, r.mean, r.var,
                                hashlib.sha1(st.tobytes()).hexdigest(), sum(h), u, o])
