@@ -1,14 +1,16 @@
 // engine_kernels.cu -- the persistent batched FPT kernel and the completion scan.
 //
-// One launch ("chunk") advances every resident lane by up to chunk_blocks blocks of kBlockSteps
-// steps (Euler-Maruyama or stochastic Heun).  A lane integrates one trajectory: Philox4x32-10 ->
-// Box-Muller -> step (Alg. 1 / 3) on a phase wrapped to [-pi, pi) with an integer winding
-// count.  Escape and upper-wrap events are caught by one running maximum per block (exact replay
-// of the rare block that reached a bound); the lower wrap (r < -pi) is applied at the end of
-// each block.  At the block end the warp votes, finished lanes publish their exact
-// result and the warp refills them -- first with suspended trajectories, then with new ids from
-// the requests' work queues (warp-aggregated atomics) -- so lanes never wait for the slowest
-// trajectory of a batch (the dynamic job assignment of Sec. III.B, Fig. 6).
+// One launch ("chunk") advances the resident lanes by chunk_blocks blocks of kBlockSteps steps
+// per warp on average (Euler-Maruyama or stochastic Heun; the last quarter of the blocks is a
+// per-CTA pool, so the warps of an SM finish together).  A lane integrates one trajectory:
+// Philox4x32-10 -> Box-Muller -> step (Alg. 1 / 3) on a phase wrapped to [-pi, pi) with an
+// integer winding count.  Escape and upper-wrap events are caught by one running maximum per
+// block (exact replay of the rare block that reached a bound); the lower wrap (r < -pi) is
+// applied at the end of each block.  At the block end the warp votes, finished lanes publish
+// their exact result (grouped in the warp, additions nobody waits for) and the warp refills them
+// -- with suspended trajectories, then ids of its reservoir, then new ids from the requests'
+// work queues (one atomic per claim) -- so lanes never wait for the slowest trajectory of a
+// batch (the dynamic job assignment of Sec. III.B, Fig. 6).
 //
 // Preemption: at the end of a launch, lanes of requests above their fair share may suspend
 // their trajectory into the request's ring (state r, v, w, step count, id); a later refill
@@ -151,13 +153,6 @@ __device__ __forceinline__ void resume_lane(Lane &L, const EngineDev &E, int s, 
     set_progress(L, S);
 }
 
-__device__ __forceinline__ void atomic_add128(unsigned long long *lo_p, unsigned long long *hi_p,
-                                              unsigned long long alo, unsigned long long ahi) {
-    const unsigned long long old = atomicAdd(lo_p, alo);
-    const unsigned long long carry = (old + alo < old) ? 1ull : 0ull;
-    if (ahi + carry) atomicAdd(hi_p, ahi + carry);
-}
-
 // Histogram bin of x = out_a + out_b k (IEEE double, separately rounded): -1 below the range,
 // hist_bins above it.
 __device__ __forceinline__ int hist_bin(const SlotDev *S, unsigned long long k) {
@@ -198,6 +193,8 @@ struct CtaView {
 __device__ __forceinline__ void emit_warp(const EngineDev &E, const CtaView &V, bool fin, int slot,
                                           unsigned long long gid, bool escaped, unsigned long long k) {
     const int lane = threadIdx.x & 31;
+    // an index out of range (checked build only) drops the trajectory's result
+    if (fin) fin = checked(E, slot >= 0 && slot < E.max_requests, kChkSlot);
     const SlotDev *S = E.slots + (fin ? slot : 0);
     unsigned long long idx = 0;
     unsigned ib = 0, row = 0;
@@ -207,9 +204,7 @@ __device__ __forceinline__ void emit_warp(const EngineDev &E, const CtaView &V, 
         ib = static_cast<unsigned>(idx / S->stop_block);
         row = S->hist_per_block ? ib : static_cast<unsigned>(idx / kHistRowIds);
         if (escaped) bin = hist_bin(S, k);
-        // an index out of range (checked build only) drops the trajectory's result
-        fin = checked(E, slot >= 0 && slot < E.max_requests, kChkSlot) &&
-              checked(E, idx < S->n_traj, kChkTraj) && checked(E, ib < S->n_idblocks, kChkIdBlock) &&
+        fin = checked(E, idx < S->n_traj, kChkTraj) && checked(E, ib < S->n_idblocks, kChkIdBlock) &&
               checked(E, row < S->hist_rows, kChkHistRow) &&
               checked(E, bin == -2 || (bin >= -1 && bin <= S->hist_bins), kChkBin);
         if (fin && S->per_traj) S->per_traj[idx] = escaped ? static_cast<long long>(k) : -1ll;
