@@ -403,12 +403,20 @@ void build_lists(fpt_engine *e, IterIO &B) {
         Request &R = *e->reqs[e->slot_req[s]];
         if (R.phase != kRunning || R.suspending) continue;
         const SlotCtl &C = e->h_ctl[s];
-        if (!fresh(e, R) || C.state != kSlotActive) continue;     // not yet launched or finishing
-        const int64_t unclaimed = C.head < R.n_traj ? static_cast<int64_t>(R.n_traj - C.head) : 0;
-        const int64_t remaining = unclaimed + std::max(C.park_avail, 0);
-        const int64_t want = std::min<int64_t>(share, C.inflight + remaining);
-        if (remaining > 0 && C.inflight < want / 2) deficit[R.dec.kind] += want - C.inflight;
-        if (C.inflight > share) over[R.dec.kind] = true;
+        // A request without a status yet was just admitted: it holds no lane, so it is starved
+        // from its first launch on and the requests above their share suspend lanes for it at
+        // the end of that launch (waiting for its first status would cost two launches).
+        const bool known = fresh(e, R);
+        if (known && C.state != kSlotActive) continue;     // finishing
+        int64_t inflight = 0, remaining = static_cast<int64_t>(R.n_traj);
+        if (known) {
+            const int64_t unclaimed = C.head < R.n_traj ? static_cast<int64_t>(R.n_traj - C.head) : 0;
+            inflight = C.inflight;
+            remaining = unclaimed + std::max(C.park_avail, 0);
+        }
+        const int64_t want = std::min<int64_t>(share, inflight + remaining);
+        if (remaining > 0 && inflight < want / 2) deficit[R.dec.kind] += want - inflight;
+        if (known && C.inflight > share) over[R.dec.kind] = true;
     }
     int64_t total_deficit = 0;
     for (int k = 0; k < kNumKinds; ++k) total_deficit += deficit[k];
