@@ -337,7 +337,7 @@ __device__ __forceinline__ void finish_lanes(Lane (&L)[T], const EngineDev &E, c
 // from the first request that has some, so no lane idles while any request has work.
 template <int T>
 __device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, const CtaView &V, int kind,
-                                       int &n_active, unsigned &cursor, unsigned b, unsigned limit) {
+                                       int &n_active, unsigned &cursor, unsigned b) {
     const int lane = threadIdx.x & 31;
     const unsigned lt = (1u << lane) - 1u;
     unsigned idle[T];
@@ -581,7 +581,7 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
                 }
             }
             finish_lanes(L, E, V, useful, n_active, n_esc, n_cens);
-            refill(L, E, V, kind_of(M, H, R), n_active, cursor, b, limit);
+            refill(L, E, V, kind_of(M, H, R), n_active, cursor, b);
             if (!__any_sync(kFull, n_active > 0)) break;
             if constexpr (!R) {
 #pragma unroll
@@ -597,6 +597,21 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
 // One trajectory per thread runs best as one CTA of 640 threads per SM: 20 warps, five per
 // scheduler, at 96 registers (measured against 512, 576, 672 and 768); two per thread as CTAs
 // of up to 256.
+// An idle warp looks for work of any kind, starting from a warp-dependent one; returns the kind
+// it took work of, or -1.
+template <int T>
+__device__ __forceinline__ int seek_work(Lane (&L)[T], const EngineDev &E, const CtaView &V, int &n_active,
+                                         unsigned &cursor, unsigned b) {
+    const unsigned warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int first = static_cast<int>(warp % kNumKinds);
+    for (int q = 0; q < kNumKinds; ++q) {
+        const int m = (first + q) % kNumKinds;
+        refill(L, E, V, m, n_active, cursor, b);
+        if (__any_sync(kFull, n_active > 0)) return m;
+    }
+    return -1;
+}
+
 template <int T>
 __global__ void __launch_bounds__(T == 1 ? 640 : 256, 1) engine_chunk_kernel(EngineDev E) {
     const unsigned nthreads = gridDim.x * blockDim.x;
@@ -616,7 +631,7 @@ __global__ void __launch_bounds__(T == 1 ? 640 : 256, 1) engine_chunk_kernel(Eng
         sh_held[s] = 0;
         sh_budget[s] = 0;
     }
-    if (threadIdx.x == 0) sh_pool = static_cast<int>((E.chunk_blocks / kPoolDiv) * (blockDim.x / 32));
+    if (threadIdx.x == 0) sh_pool = 0;
     if (threadIdx.x < 32) {
         sh_res_slot[threadIdx.x] = -1;
         sh_res_cnt[threadIdx.x] = 0;
@@ -679,18 +694,18 @@ __global__ void __launch_bounds__(T == 1 ? 640 : 256, 1) engine_chunk_kernel(Eng
     unsigned cursor = E.warp_cursor[warp];
     unsigned long long useful = 0;
     unsigned n_esc = 0, n_cens = 0;
-    if (kind >= 0) refill(L, E, V, kind, n_active, cursor, 0u, 0u);
     unsigned b = 0;
+    if (kind >= 0) refill(L, E, V, kind, n_active, cursor, 0u);
+    else kind = seek_work(L, E, V, n_active, cursor, 0u);
+    // The CTA's pool holds the last 1/kPoolDiv of the launch's blocks of every warp that has work
+    // now, so a CTA whose warps are partly idle (fewer trajectories than lanes) gives its busy
+    // warps as many blocks as a full CTA does, and all CTAs end together.
+    if (lane == 0 && kind >= 0) atomicAdd(&sh_pool, static_cast<int>(E.chunk_blocks / kPoolDiv));
+    __syncthreads();
     unsigned limit = E.chunk_blocks - E.chunk_blocks / kPoolDiv;
     while (b < limit || grant(V, limit)) {
         if (kind < 0) {
-            // an idle warp looks for work of any kind, starting from a warp-dependent one
-            const int first = static_cast<int>(warp % kNumKinds);
-            for (int q = 0; q < kNumKinds && kind < 0; ++q) {
-                const int m = (first + q) % kNumKinds;
-                refill(L, E, V, m, n_active, cursor, b, limit);
-                if (__any_sync(kFull, n_active > 0)) kind = m;
-            }
+            kind = seek_work(L, E, V, n_active, cursor, b);
             if (kind < 0) break;
         }
         switch (kind) {
