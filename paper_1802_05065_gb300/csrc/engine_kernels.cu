@@ -41,7 +41,7 @@ struct Lane {
     unsigned budget;      // blocks to the next event: step budget end, bias re-base, carry
     float gb, Jf;         // bias base and 4 x blocks since the base (exact)
     float dt, A, amp, bmc, nudt;
-    PhiloxLane P;         // the trajectory's Philox stream (round keys, round-0 constants)
+    PhiloxLane P;         // the trajectory's Philox stream (round keys, fixed words of rounds 0-2)
 };
 
 __device__ __forceinline__ float qnan_f() { return __int_as_float(0x7FFFFFFF); }
@@ -575,9 +575,10 @@ __device__ __forceinline__ unsigned run_blocks(Lane (&L)[T], const EngineDev &E,
                     }
                 }
                 if (L[t].r < -kPiF) wrap_down(L[t], E);
-                if (L[t].slot >= 0 && L[t].c_lo == 0u) {   // 2^32-block carry
+                if (L[t].slot >= 0 && L[t].c_lo == 0u) {   // 2^32-block carry: new fixed words
                     L[t].c_hi += 1u;
-                    philox_lane_set_hi(L[t].P, L[t].c_hi - 1u, L[t].c_hi);
+                    const SlotDev *S = E.slots + L[t].slot;
+                    philox_lane_init(L[t].P, S->key0, S->key1, L[t].c_hi, L[t].gid_lo, L[t].gid_hi);
                 }
             }
             finish_lanes(L, E, V, useful, n_active, n_esc, n_cens);

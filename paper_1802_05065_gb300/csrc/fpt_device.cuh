@@ -1,7 +1,7 @@
 // fpt_device.cuh -- device primitives of the FPT hot path (sm_103a).
 //
 //   philox4x32_10   counter-based generator (Salmon et al., SC'11), all in registers
-//   PhiloxLane      the same generator with round 0's block-independent half kept per lane
+//   PhiloxLane      the same generator with the words of rounds 0-2 that no block changes kept per lane
 //   bm_pair_f32     Box-Muller (Sec. III.B, nrand) in single precision, noise-scaled
 //   bm_pair_f64     Box-Muller in double precision, same arithmetic order as the FP64 oracle
 //   step_f32<M,H>   one Euler-Maruyama step of Alg. 1 / Alg. 3 (H = 0) or one stochastic Heun
@@ -27,45 +27,63 @@ constexpr float kPiF = 3.14159265358979323846f;
 constexpr float kTwoPiF = 6.28318530717958647692f;
 
 // Philox4x32-10 of one trajectory, prepared for the many blocks it draws.  Counter words
-// (c0, c1, c2, c3) = (block lo, block hi, trajectory lo, trajectory hi): round 0 multiplies c2
-// by M1 and c0 by M0, so its outputs x' = hi(M1 c2) ^ c1 ^ k0, y' = lo(M1 c2) and the mask
-// c3 ^ k1 of z' = hi(M0 c0) ^ c3 ^ k1 are the same for every block that shares the high word.
-// They are kept per lane with the round keys of rounds 1..9; a block then costs one wide
-// multiply less per call.  Same output as philox4x32_10.
+// (c0, c1, c2, c3) = (block lo, block hi, trajectory lo, trajectory hi), key (k0, k1); round r
+// uses the key (k0 + r W0, k1 + r W1) and maps (x, y, z, w) to
+// (hi(M1 z) ^ y ^ k0r, lo(M1 z), hi(M0 x) ^ w ^ k1r, lo(M0 x)).  Only c0 changes from block to
+// block (c1 only on a carry of 2^32 blocks), so for every block of the trajectory:
+//   round 0: x1 = hi(M1 c2) ^ c1 ^ k0 and y1 = lo(M1 c2) are fixed; z1 = hi(M0 c0) ^ (c3 ^ k1)
+//            takes a fixed mask;
+//   round 1: its product M0 x1 is fixed, so z2 = hi(M0 x1) ^ w1 ^ (k1 + W1) and w2 = lo(M0 x1)
+//            take fixed words, as does x2 = hi(M1 z1) ^ (y1 ^ (k0 + W0));
+//   round 2: z3 = hi(M0 x2) ^ (w2 ^ (k1 + 2 W1)), with w2 fixed.
+// Those fixed words, with their round keys folded in, are kept per lane with the round keys of
+// rounds 2..9 (k0) and 3..9 (k1): a call costs one wide multiply in round 0 and one in round 1.
+// Same output as philox4x32_10.
 struct PhiloxLane {
-    uint32_t ka[9], kb[9];    // round keys k + r W, rounds 1..9
-    uint32_t x0, y0, w1;      // round-0 outputs x', y' and the mask c3 ^ k1
+    uint32_t ka[8];   // k0 + r W0, rounds 2..9
+    uint32_t kb[7];   // k1 + r W1, rounds 3..9
+    uint32_t m0;      // round 0: c3 ^ k1
+    uint32_t x1m;     // round 1: y1 ^ (k0 + W0)
+    uint32_t z1m;     // round 1: hi(M0 x1) ^ (k1 + W1)
+    uint32_t z2m;     // round 2: lo(M0 x1) ^ (k1 + 2 W1)
 };
 
-__device__ __forceinline__ void philox_lane_init(PhiloxLane &P, uint32_t k0, uint32_t k1,
-                                                 uint32_t c_hi, uint32_t t_lo, uint32_t t_hi) {
+__host__ __device__ __forceinline__ void philox_lane_init(PhiloxLane &P, uint32_t k0, uint32_t k1,
+                                                          uint32_t c_hi, uint32_t t_lo, uint32_t t_hi) {
 #pragma unroll
-    for (int r = 1; r < 10; ++r) {
-        P.ka[r - 1] = k0 + static_cast<uint32_t>(r) * kPhiloxW0;
-        P.kb[r - 1] = k1 + static_cast<uint32_t>(r) * kPhiloxW1;
-    }
+    for (int r = 2; r < 10; ++r) P.ka[r - 2] = k0 + static_cast<uint32_t>(r) * kPhiloxW0;
+#pragma unroll
+    for (int r = 3; r < 10; ++r) P.kb[r - 3] = k1 + static_cast<uint32_t>(r) * kPhiloxW1;
     const uint64_t p1 = static_cast<uint64_t>(kPhiloxM1) * t_lo;
-    P.x0 = static_cast<uint32_t>(p1 >> 32) ^ c_hi ^ k0;
-    P.y0 = static_cast<uint32_t>(p1);
-    P.w1 = t_hi ^ k1;
-}
-
-// The high counter word changed from old_hi to new_hi (a carry of the block count).
-__device__ __forceinline__ void philox_lane_set_hi(PhiloxLane &P, uint32_t old_hi, uint32_t new_hi) {
-    P.x0 ^= old_hi ^ new_hi;
+    const uint32_t x1 = static_cast<uint32_t>(p1 >> 32) ^ c_hi ^ k0;
+    const uint32_t y1 = static_cast<uint32_t>(p1);
+    const uint64_t q0 = static_cast<uint64_t>(kPhiloxM0) * x1;          // round 1's fixed product
+    P.m0 = t_hi ^ k1;
+    P.x1m = y1 ^ (k0 + kPhiloxW0);
+    P.z1m = static_cast<uint32_t>(q0 >> 32) ^ (k1 + kPhiloxW1);
+    P.z2m = static_cast<uint32_t>(q0) ^ (k1 + 2u * kPhiloxW1);
 }
 
 // Words of block c_lo + h for h < 4 with c_lo a multiple of 4 (no carry into the high word):
 // round 0's product M0 (c_lo + h) is formed as the wide multiply-add M0 c_lo + M0 h.
-__device__ __forceinline__ uint4 philox_lane_block(const PhiloxLane &P, uint32_t c_lo, uint32_t h) {
+__host__ __device__ __forceinline__ uint4 philox_lane_block(const PhiloxLane &P, uint32_t c_lo, uint32_t h) {
     const uint64_t p0 = static_cast<uint64_t>(kPhiloxM0) * c_lo + static_cast<uint64_t>(kPhiloxM0) * h;
-    uint4 c = make_uint4(P.x0, P.y0, static_cast<uint32_t>(p0 >> 32) ^ P.w1, static_cast<uint32_t>(p0));
+    const uint32_t z1 = static_cast<uint32_t>(p0 >> 32) ^ P.m0, w1 = static_cast<uint32_t>(p0);
+    // round 1 (x1, y1 and the product M0 x1 are in the masks)
+    const uint64_t q1 = static_cast<uint64_t>(kPhiloxM1) * z1;
+    const uint32_t x2 = static_cast<uint32_t>(q1 >> 32) ^ P.x1m, y2 = static_cast<uint32_t>(q1);
+    const uint32_t z2 = P.z1m ^ w1;
+    // round 2 (w2 is in the mask z2m)
+    const uint64_t r0 = static_cast<uint64_t>(kPhiloxM0) * x2;
+    const uint64_t r1 = static_cast<uint64_t>(kPhiloxM1) * z2;
+    uint4 c = make_uint4(static_cast<uint32_t>(r1 >> 32) ^ y2 ^ P.ka[0], static_cast<uint32_t>(r1),
+                         static_cast<uint32_t>(r0 >> 32) ^ P.z2m, static_cast<uint32_t>(r0));
 #pragma unroll
-    for (int round = 1; round < 10; ++round) {
-        const uint64_t q0 = static_cast<uint64_t>(kPhiloxM0) * c.x;
-        const uint64_t q1 = static_cast<uint64_t>(kPhiloxM1) * c.z;
-        c = make_uint4(static_cast<uint32_t>(q1 >> 32) ^ c.y ^ P.ka[round - 1], static_cast<uint32_t>(q1),
-                       static_cast<uint32_t>(q0 >> 32) ^ c.w ^ P.kb[round - 1], static_cast<uint32_t>(q0));
+    for (int round = 3; round < 10; ++round) {
+        const uint64_t a0 = static_cast<uint64_t>(kPhiloxM0) * c.x;
+        const uint64_t a1 = static_cast<uint64_t>(kPhiloxM1) * c.z;
+        c = make_uint4(static_cast<uint32_t>(a1 >> 32) ^ c.y ^ P.ka[round - 2], static_cast<uint32_t>(a1),
+                       static_cast<uint32_t>(a0 >> 32) ^ c.w ^ P.kb[round - 3], static_cast<uint32_t>(a0));
     }
     return c;
 }
