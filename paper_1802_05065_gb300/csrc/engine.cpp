@@ -280,6 +280,15 @@ fpt_status admit(fpt_engine *e) {
         S.nblocks = (d.max_steps + 3) / 4;
         S.gamma0 = d.gamma0;
         S.nudt_d = d.nudt;
+        // the bias base and event countdown of a trajectory at block 0, as the kernel's
+        // set_progress forms them (c = c_base = 0; the re-base and carry counts are whole)
+        S.gb0 = static_cast<float>(d.gamma0 + d.nudt * static_cast<double>(0ull));
+        {
+            const uint64_t to_end = S.nblocks, to_base = kRebaseBlocks, to_carry = 0x100000000ull;
+            uint64_t m = to_end < to_base ? to_end : to_base;
+            m = m < to_carry ? m : to_carry;
+            S.budget0 = static_cast<uint32_t>((m + kBlockPhilox - 1) / kBlockPhilox);
+        }
         S.output = d.output;
         S.hist_bins = d.hist_bins;
         S.out_a = d.out_a;
@@ -290,6 +299,7 @@ fpt_status admit(fpt_engine *e) {
         S.stop_rse = R.params.stop_rse;
         S.stop_block = R.stop_block;
         S.n_idblocks = R.n_idblocks;
+        id_block_magic(R.stop_block, S.ib_magic, S.ib_shift);
         S.acc = R.acc;
         S.hist = R.hist;
         S.hist_per_block = R.params.stop_rse > 0.0 ? 1 : 0;

@@ -14,6 +14,12 @@
 
 #include <cstdint>
 
+#if defined(__CUDACC__)
+#define FPT_HD __host__ __device__
+#else
+#define FPT_HD
+#endif
+
 namespace fpt {
 
 enum : int { kSlotFree = 0, kSlotActive = 1, kSlotFinished = 2, kSlotCancelled = 3 };
@@ -59,6 +65,28 @@ struct IdBlockAcc {
     unsigned long long s2[3];   // limbs of the sum of squared escape steps
 };
 
+// Exact quotient n / d for 0 <= n < 2^40 (trajectory indices; n_traj <= 2^40) and a 32-bit
+// divisor d >= 1 by one multiply: with l = ceil(log2 d) and m = ceil(2^(40 + l) / d) < 2^41 + 1,
+// floor(n / d) = floor(n m / 2^(40 + l)) (Granlund & Montgomery, "Division by invariant integers
+// using multiplication", 1994, Thm. 4.2 with N = 40: 2^(N+l) <= m d <= 2^(N+l) + 2^l).
+inline void id_block_magic(uint32_t d, uint64_t &m, int32_t &s) {
+    int l = 0;
+    while ((1ull << l) < d) ++l;
+    s = 40 + l;
+    const unsigned __int128 p = static_cast<unsigned __int128>(1) << s;
+    m = static_cast<uint64_t>((p + d - 1) / d);
+}
+
+FPT_HD inline uint64_t id_block_quot(uint64_t n, uint64_t m, int32_t s) {
+#if defined(__CUDA_ARCH__)
+    const uint64_t hi = __umul64hi(n, m);
+#else
+    const uint64_t hi = static_cast<uint64_t>((static_cast<unsigned __int128>(n) * m) >> 64);
+#endif
+    const uint64_t lo = n * m;
+    return s >= 64 ? hi >> (s - 64) : (lo >> s) | (hi << (64 - s));   // 40 <= s <= 72
+}
+
 struct SlotDev {
     // single-precision step constants
     float dt, A, amp, bmc, nudt, v0, r0, eb0;
@@ -67,12 +95,16 @@ struct SlotDev {
     // trajectories and budget
     uint64_t traj_offset, n_traj, max_steps, nblocks;   // nblocks = ceil(max_steps / 4)
     double gamma0, nudt_d;                               // double bias ramp
+    float gb0;                // bias base of a trajectory at block 0 (set_progress at c = 0)
+    uint32_t budget0;         // its event countdown at block 0
     // observable and histogram: x = out_a + out_b k
     int32_t output, hist_bins;
     double out_a, out_b, hist_lo, hist_hi, hist_inv_w;
     // prefix stop rule
     double stop_rse;
     uint32_t stop_block, n_idblocks;
+    uint64_t ib_magic;        // id block of index i = id_block_quot(i, ib_magic, ib_shift)
+    int32_t ib_shift;
     IdBlockAcc *acc;
     unsigned int *hist;        // rows x hist_bins
     int32_t hist_per_block;    // 1: row = id block (stop rule), 0: row = id / kHistRowIds

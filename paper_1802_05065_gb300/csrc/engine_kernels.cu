@@ -133,7 +133,9 @@ __device__ __forceinline__ void init_lane(Lane &L, const EngineDev &E, int s, un
     L.hb = fminf(S->eb0, kPiF);
     L.esc = -1;
     load_consts(L, S);
-    set_progress(L, S);
+    L.gb = S->gb0;       // set_progress at c = 0, formed on the host
+    L.Jf = 0.0f;
+    L.budget = S->budget0;
 }
 
 // Continue a suspended trajectory exactly where it stopped.
@@ -195,13 +197,14 @@ __device__ __forceinline__ void emit_warp(const EngineDev &E, const CtaView &V, 
     const int lane = threadIdx.x & 31;
     // an index out of range (checked build only) drops the trajectory's result
     if (fin) fin = checked(E, slot >= 0 && slot < E.max_requests, kChkSlot);
+    if (!__any_sync(kFull, fin)) return;   // an event block without a finished trajectory
     const SlotDev *S = E.slots + (fin ? slot : 0);
     unsigned long long idx = 0;
     unsigned ib = 0, row = 0;
     int bin = -2;
     if (fin) {
         idx = gid - S->traj_offset;
-        ib = static_cast<unsigned>(idx / S->stop_block);
+        ib = static_cast<unsigned>(id_block_quot(idx, S->ib_magic, S->ib_shift));
         row = S->hist_per_block ? ib : static_cast<unsigned>(idx / kHistRowIds);
         if (escaped) bin = hist_bin(S, k);
         fin = checked(E, idx < S->n_traj, kChkTraj) && checked(E, ib < S->n_idblocks, kChkIdBlock) &&
