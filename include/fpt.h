@@ -146,6 +146,12 @@ typedef struct {
     uint32_t chunk_steps;       /* steps per resident-kernel launch, multiple of 16 (0 = 16384) */
     int32_t service_thread;     /* 1: an engine thread drives the GPU; 0: caller calls fpt_step */
     int32_t use_graph;          /* 1: replay a CUDA graph per iteration (default 1) */
+    uint32_t young_chunk_steps; /* steps per launch while a request of at most as many
+                                   trajectories as lanes was admitted within the last 16
+                                   launches: shorter quanta for new small requests, which wait
+                                   fewer steps of the others for admission, lanes and their
+                                   result (multiple of 16, <= chunk_steps; 0 = chunk_steps).
+                                   Results do not depend on it. */
 } fpt_engine_config;
 
 typedef struct {

@@ -68,6 +68,7 @@ class EngineConfig(ctypes.Structure):
         ("threads_per_block", ctypes.c_int32), ("blocks_per_sm", ctypes.c_int32),
         ("traj_per_thread", ctypes.c_int32), ("chunk_steps", ctypes.c_uint32),
         ("service_thread", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+        ("young_chunk_steps", ctypes.c_uint32),
     ]
 
 

@@ -132,7 +132,8 @@ size_t request_bytes(const fpt_params &p, uint64_t n_traj, uint32_t B, unsigned 
 // events and its graph.  Two alternate.
 struct IterIO {
     int *caps = nullptr, *act = nullptr, *act_count = nullptr;
-    int *preempt = nullptr, *flags = nullptr;   // flags: vacate[kNumKinds], strict, claim_warps
+    int *preempt = nullptr, *flags = nullptr;   // flags: vacate[kNumKinds], strict, claim_warps,
+                                                // blocks per warp of the launch
     SlotCtl *ctl = nullptr;                     // status download target
     unsigned long long *counters = nullptr;     // counters download target
     cudaEvent_t k0 = nullptr, k1 = nullptr;     // around the resident kernel
@@ -140,7 +141,15 @@ struct IterIO {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     uint64_t seq = 0;                           // number of the iteration that used these buffers
+    unsigned chunk_blocks = 0;                  // blocks per warp of that launch
 };
+
+// Flags uploaded with each launch: vacate[kNumKinds], strict, claim_warps, blocks per warp.
+constexpr int kNumFlags = kNumKinds + 3;
+
+// Launches after its admission during which a request that fits in the lanes counts as young
+// (the launch length is then the engine's young_chunk_steps).
+constexpr uint64_t kYoungLaunches = 16;
 
 struct fpt_engine {
     fpt_engine_config cfg{};
@@ -149,6 +158,8 @@ struct fpt_engine {
     bool own_stream = false;
     int sms = 0, grid = 0, block = 256, T = 2, maxr = 256;
     unsigned lanes = 0, chunk_blocks = 0;
+    unsigned young_blocks = 0;    // blocks per warp of a launch while a small request is young
+    uint64_t lane_slots = 0;      // lanes x steps offered by the processed launches
     // device
     SlotDev *d_slots = nullptr;
     SlotCtl *d_ctl = nullptr;
@@ -405,6 +416,20 @@ void build_lists(fpt_engine *e, IterIO &B) {
         B.flags[kNumKinds + 1] =
             static_cast<int>(std::min<int64_t>(std::max<int64_t>(warps, 1), e->block / 32));
     }
+    // Launch length: short while a request that fits in the lanes is young, so it waits fewer
+    // steps of the others for its admission, its lanes and the status that reports its result.
+    B.chunk_blocks = e->chunk_blocks;
+    if (e->young_blocks)
+        for (int s = 0; s < e->maxr; ++s) {
+            if (!e->slot_req[s]) continue;
+            const Request &R = *e->reqs[e->slot_req[s]];
+            if (R.phase == kRunning && !R.suspending && R.n_traj <= e->lanes &&
+                e->enq_seq < R.admit_seq + kYoungLaunches) {
+                B.chunk_blocks = e->young_blocks;
+                break;
+            }
+        }
+    B.flags[kNumKinds + 2] = static_cast<int>(B.chunk_blocks);
     if (active < 2) return;
     int64_t deficit[kNumKinds] = {};
     bool over[kNumKinds] = {};
@@ -457,7 +482,7 @@ fpt_status enqueue_iteration(fpt_engine *e, IterIO &B) {
     }
     CK(cudaMemcpyAsync(e->d_caps, B.caps, e->maxr * sizeof(int), cudaMemcpyHostToDevice, e->stream));
     CK(cudaMemcpyAsync(e->d_preempt, B.preempt, e->maxr * sizeof(int), cudaMemcpyHostToDevice, e->stream));
-    CK(cudaMemcpyAsync(e->d_vacate, B.flags, (kNumKinds + 2) * sizeof(int), cudaMemcpyHostToDevice,
+    CK(cudaMemcpyAsync(e->d_vacate, B.flags, kNumFlags * sizeof(int), cudaMemcpyHostToDevice,
                        e->stream));
     CK(cudaMemcpyAsync(e->d_act, B.act, kNumKinds * e->maxr * sizeof(int), cudaMemcpyHostToDevice,
                        e->stream));
@@ -537,6 +562,7 @@ fpt_status complete_oldest(fpt_engine *e) {
         e->status_seq = B.seq;
         process_status(e);
         ++e->iterations;
+        e->lane_slots += static_cast<uint64_t>(e->lanes) * B.chunk_blocks * kBlockSteps;
         e->kernel_ms += ms;
     }
     e->flight[0] = e->flight[1];
@@ -695,6 +721,10 @@ fpt_status create_impl(const fpt_engine_config *cfg_in, fpt_engine *e) {
     if (chunk % kBlockSteps || chunk > (1u << 24))
         return fail(e, FPT_EINVAL, "chunk_steps: multiple of 16 (the kernel's block), <= 2^24");
     e->chunk_blocks = chunk / kBlockSteps;
+    if (cfg.young_chunk_steps % kBlockSteps || cfg.young_chunk_steps > chunk)
+        return fail(e, FPT_EINVAL, "young_chunk_steps: multiple of 16, <= chunk_steps");
+    e->young_blocks = cfg.young_chunk_steps / kBlockSteps;
+    if (e->young_blocks == e->chunk_blocks) e->young_blocks = 0;
     CK(cudaDeviceGetAttribute(&e->sms, cudaDevAttrMultiProcessorCount, cfg.device));
     int bps = 0;
     CK(engine_chunk_occupancy(e->T, e->block, &bps));
@@ -719,9 +749,9 @@ fpt_status create_impl(const fpt_engine_config *cfg_in, fpt_engine *e) {
     CK(cudaMalloc(&e->d_act, kNumKinds * R * sizeof(int)));
     CK(cudaMalloc(&e->d_act_count, kNumKinds * sizeof(int)));
     CK(cudaMalloc(&e->d_preempt, R * sizeof(int)));
-    CK(cudaMalloc(&e->d_vacate, (kNumKinds + 2) * sizeof(int)));   // vacate[kNumKinds], strict, claim
+    CK(cudaMalloc(&e->d_vacate, kNumFlags * sizeof(int)));   // vacate[kNumKinds], strict, claim, chunk
     CK(cudaMemsetAsync(e->d_preempt, 0, R * sizeof(int), e->stream));
-    CK(cudaMemsetAsync(e->d_vacate, 0, (kNumKinds + 2) * sizeof(int), e->stream));
+    CK(cudaMemsetAsync(e->d_vacate, 0, kNumFlags * sizeof(int), e->stream));
     const size_t L = e->lanes;
     CK(cudaMalloc(&e->d_lane_mem, L * 4 * 10));
     const unsigned nwarps = static_cast<unsigned>(e->grid) * e->block / 32;
@@ -762,14 +792,14 @@ fpt_status create_impl(const fpt_engine_config *cfg_in, fpt_engine *e) {
         CK(cudaMallocHost(&B.act, kNumKinds * R * sizeof(int)));
         CK(cudaMallocHost(&B.act_count, kNumKinds * sizeof(int)));
         CK(cudaMallocHost(&B.preempt, R * sizeof(int)));
-        CK(cudaMallocHost(&B.flags, (kNumKinds + 2) * sizeof(int)));
+        CK(cudaMallocHost(&B.flags, kNumFlags * sizeof(int)));
         CK(cudaMallocHost(&B.ctl, R * sizeof(SlotCtl)));
         CK(cudaMallocHost(&B.counters, kCntCount * sizeof(unsigned long long)));
         std::memset(B.caps, 0, R * sizeof(int));
         std::memset(B.act, 0, kNumKinds * R * sizeof(int));
         std::memset(B.act_count, 0, kNumKinds * sizeof(int));
         std::memset(B.preempt, 0, R * sizeof(int));
-        std::memset(B.flags, 0, (kNumKinds + 2) * sizeof(int));
+        std::memset(B.flags, 0, kNumFlags * sizeof(int));
         std::memset(B.ctl, 0, R * sizeof(SlotCtl));
         std::memset(B.counters, 0, kCntCount * sizeof(unsigned long long));
         CK(cudaEventCreate(&B.k0));
@@ -786,6 +816,7 @@ fpt_status create_impl(const fpt_engine_config *cfg_in, fpt_engine *e) {
     d.vacate = e->d_vacate;
     d.strict = e->d_vacate + kNumKinds;
     d.claim_warps = e->d_vacate + kNumKinds + 1;
+    d.chunk_now = e->d_vacate + kNumKinds + 2;
     d.act_count = e->d_act_count;
     d.warp_kind = e->d_warp_kind;
     d.warp_cursor = e->d_warp_cursor;
@@ -1194,7 +1225,7 @@ extern "C" fpt_status fpt_get_counters(fpt_engine *e, fpt_engine_counters *out) 
     out->escapes = e->h_counters[kCntEscapes];
     out->censored = e->h_counters[kCntCensored];
     out->check_flags = e->h_counters[kCntCheck];
-    out->lane_step_slots = e->iterations * static_cast<uint64_t>(e->lanes) * e->chunk_blocks * kBlockSteps;
+    out->lane_step_slots = e->lane_slots;
     out->lanes = e->lanes;
     out->grid = e->grid;
     out->block = e->block;

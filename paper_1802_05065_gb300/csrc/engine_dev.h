@@ -147,13 +147,14 @@ struct EngineDev {
     const int *strict;      // [1] 1: never exceed the caps (someone is starved)
     const int *claim_warps; // [1] warps of each CTA (counted from warp 0) that claim new work:
                             // when there is less work than lanes it is spread over every SM
+    const int *chunk_now;   // [1] blocks per warp of this launch (<= chunk_blocks)
     const int *act_list;    // [kNumKinds][max_requests] claimable slots per kind
     const int *act_count;   // [kNumKinds]
     LaneSoA lanes;
     int *warp_kind;         // kind each warp currently integrates (-1 idle)
     unsigned int *warp_cursor;
     unsigned long long *counters;
-    unsigned int chunk_blocks;
+    unsigned int chunk_blocks;   // blocks per warp of a full launch
     int max_requests;
     unsigned int n_lanes;   // threads x trajectories per thread (lane state entries)
 };

@@ -1,8 +1,9 @@
 // engine_kernels.cu -- the persistent batched FPT kernel and the completion scan.
 //
-// One launch ("chunk") advances the resident lanes by chunk_blocks blocks of kBlockSteps steps
-// per warp on average (Euler-Maruyama or stochastic Heun; the last quarter of the blocks is a
-// per-CTA pool, so the warps of an SM finish together).  A lane integrates one trajectory:
+// One launch ("chunk") advances the resident lanes by the launch's blocks of kBlockSteps steps
+// per warp on average (chunk_blocks, or fewer while a small request is new; Euler-Maruyama or
+// stochastic Heun; the last quarter of the blocks is a per-CTA pool, so the warps of an SM
+// finish together).  A lane integrates one trajectory:
 // Philox4x32-10 -> Box-Muller -> step (Alg. 1 / 3) on a phase wrapped to [-pi, pi) with an
 // integer winding count.  Escape and upper-wrap events are caught by one running maximum per
 // block (exact replay of the rare block that reached a bound); the lower wrap (r < -pi) is
@@ -183,6 +184,7 @@ struct CtaView {
     unsigned long long *res_base;   // ... and first id (ids res_base .. res_base + res_cnt - 1)
     int *started;                // per warp: trajectories it started in this launch
     int *pool;                   // blocks of this launch not yet taken by a warp of the CTA
+    unsigned chunk;              // blocks per warp of this launch
 };
 
 // Publish the trajectories finishing in this warp at this block end (warp-collective: every lane
@@ -412,7 +414,7 @@ __device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, const C
                     int extra = 0;
                     if (V.res_cnt[wl] == 0 && !capped && b > 0 && 8u * static_cast<unsigned>(V.started[wl]) >= b) {
                         const unsigned long long expect =
-                            static_cast<unsigned long long>(V.started[wl]) * (E.chunk_blocks > b ? E.chunk_blocks - b : 0u) / b;
+                            static_cast<unsigned long long>(V.started[wl]) * (V.chunk > b ? V.chunk - b : 0u) / b;
                         const int want_extra = expect < static_cast<unsigned long long>(kReserveIds)
                                                    ? static_cast<int>(expect) : kReserveIds;
                         if (want_extra > 0) {
@@ -629,7 +631,10 @@ __global__ void __launch_bounds__(T == 1 ? 640 : 256, 1) engine_chunk_kernel(Eng
     __shared__ int sh_res_slot[32], sh_res_cnt[32], sh_started[32];   // a CTA has at most 32 warps
     __shared__ unsigned long long sh_res_base[32];
     __shared__ int sh_pool;
-    const CtaView V{sh_ok, sh_held, sh_budget, sh_res_slot, sh_res_cnt, sh_res_base, sh_started, &sh_pool};
+    // blocks per warp of this launch: the engine's full launch or a shorter one it chose
+    unsigned chunk = static_cast<unsigned>(*E.chunk_now);
+    if (chunk == 0u || chunk > E.chunk_blocks) chunk = E.chunk_blocks;
+    const CtaView V{sh_ok, sh_held, sh_budget, sh_res_slot, sh_res_cnt, sh_res_base, sh_started, &sh_pool, chunk};
     for (int s = threadIdx.x; s < E.max_requests; s += blockDim.x) {
         sh_ok[s] = 0u;
         sh_held[s] = 0;
@@ -704,9 +709,9 @@ __global__ void __launch_bounds__(T == 1 ? 640 : 256, 1) engine_chunk_kernel(Eng
     // The CTA's pool holds the last 1/kPoolDiv of the launch's blocks of every warp that has work
     // now, so a CTA whose warps are partly idle (fewer trajectories than lanes) gives its busy
     // warps as many blocks as a full CTA does, and all CTAs end together.
-    if (lane == 0 && kind >= 0) atomicAdd(&sh_pool, static_cast<int>(E.chunk_blocks / kPoolDiv));
+    if (lane == 0 && kind >= 0) atomicAdd(&sh_pool, static_cast<int>(chunk / kPoolDiv));
     __syncthreads();
-    unsigned limit = E.chunk_blocks - E.chunk_blocks / kPoolDiv;
+    unsigned limit = chunk - chunk / kPoolDiv;
     while (b < limit || grant(V, limit)) {
         if (kind < 0) {
             kind = seek_work(L, E, V, n_active, cursor, b);
