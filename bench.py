@@ -346,19 +346,22 @@ def serving_loads(pkg, dev, n_requests):
         capacity, capacity = the engine's throughput on this mix while saturated.
     Offered load = trajectory-steps the requests need, each measured alone in an idle engine,
     / arrival span.  Slowdown = latency / the request's latency alone.  Four requests (the
-    cheapest ones) are also run by the plain FP64 kernel on the ids their FP32 result used."""
+    cheapest ones) are also run by the plain FP64 kernel on the ids their FP32 result used.
+    Launches are 4096 steps, 1024 while a request that fits in the lanes is new (the engine's
+    young_chunk_steps), alone and in the stream alike."""
     import workloads
     from paper_1802_05065_gb300 import serving as _srv
-    chunk = 4096
+    chunk, young = 4096, 1024
+    kw = {"young_chunk_steps": young}
     stream = workloads.serving_stream(n_requests=n_requests)
-    alone = _srv.run_alone(stream, device=dev, chunk_steps=chunk)
+    alone = _srv.run_alone(stream, device=dev, chunk_steps=chunk, engine_kw=kw)
     lat_alone = [a["latency_s"] for a in alone]
     work = float(sum(a["steps"] for a in alone))
     span = stream[-1][0]
 
     def one(st, label):
         out = _srv.run_stream(st, device=dev, chunk_steps=chunk, timeout_s=600.0,
-                              keep_results=True)
+                              keep_results=True, engine_kw=kw)
         res = out.pop("results")
         lat = [r.latency_s for r in res if r is not None]
         al = [la for la, r in zip(lat_alone, res) if r is not None]
@@ -405,7 +408,7 @@ def serving_loads(pkg, dev, n_requests):
                      "fp64_plain_s": a.elapsed_time(b) / 1e3})
     return {"stream": f"{n_requests} requests drawn as in the uneven batch, 2^12..2^20 "
                       "trajectories, 1 % RSE stop rule, Poisson arrivals",
-            "chunk_steps": chunk, "capacity_steps_per_s": capacity,
+            "chunk_steps": chunk, "young_chunk_steps": young, "capacity_steps_per_s": capacity,
             "work_steps": work, "alone_total_s": sum(lat_alone), "loads": loads,
             "fp32_vs_fp64": vs64}
 

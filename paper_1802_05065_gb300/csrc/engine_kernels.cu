@@ -184,7 +184,6 @@ struct CtaView {
     unsigned long long *res_base;   // ... and first id (ids res_base .. res_base + res_cnt - 1)
     int *started;                // per warp: trajectories it started in this launch
     int *pool;                   // blocks of this launch not yet taken by a warp of the CTA
-    unsigned chunk;              // blocks per warp of this launch
 };
 
 // Publish the trajectories finishing in this warp at this block end (warp-collective: every lane
@@ -405,8 +404,9 @@ __device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, const C
                     got += rt;
                 }
                 // 3. the queue head, with more for the reservoir when it is free: as many as this
-                //    warp is expected to start in the rest of the launch at its rate so far (at
-                //    most kReserveIds, none while caps are enforced), within the CTA's budget.
+                //    warp is expected to start in the rest of a full launch at its rate so far
+                //    (at most kReserveIds, none while caps are enforced), within the CTA's budget;
+                //    in a shorter launch the surplus goes back to the ring at its end.
                 //    Only warps that start a trajectory at least every 8 blocks keep one: for
                 //    long trajectories the ids would mostly return to the ring unused.
                 if (want > got && (V.ok[s] & 1u)) {
@@ -414,7 +414,7 @@ __device__ __forceinline__ void refill(Lane (&L)[T], const EngineDev &E, const C
                     int extra = 0;
                     if (V.res_cnt[wl] == 0 && !capped && b > 0 && 8u * static_cast<unsigned>(V.started[wl]) >= b) {
                         const unsigned long long expect =
-                            static_cast<unsigned long long>(V.started[wl]) * (V.chunk > b ? V.chunk - b : 0u) / b;
+                            static_cast<unsigned long long>(V.started[wl]) * (E.chunk_blocks > b ? E.chunk_blocks - b : 0u) / b;
                         const int want_extra = expect < static_cast<unsigned long long>(kReserveIds)
                                                    ? static_cast<int>(expect) : kReserveIds;
                         if (want_extra > 0) {
@@ -631,16 +631,19 @@ __global__ void __launch_bounds__(T == 1 ? 640 : 256, 1) engine_chunk_kernel(Eng
     __shared__ int sh_res_slot[32], sh_res_cnt[32], sh_started[32];   // a CTA has at most 32 warps
     __shared__ unsigned long long sh_res_base[32];
     __shared__ int sh_pool;
-    // blocks per warp of this launch: the engine's full launch or a shorter one it chose
-    unsigned chunk = static_cast<unsigned>(*E.chunk_now);
-    if (chunk == 0u || chunk > E.chunk_blocks) chunk = E.chunk_blocks;
-    const CtaView V{sh_ok, sh_held, sh_budget, sh_res_slot, sh_res_cnt, sh_res_base, sh_started, &sh_pool, chunk};
+    __shared__ unsigned sh_chunk;
+    const CtaView V{sh_ok, sh_held, sh_budget, sh_res_slot, sh_res_cnt, sh_res_base, sh_started, &sh_pool};
     for (int s = threadIdx.x; s < E.max_requests; s += blockDim.x) {
         sh_ok[s] = 0u;
         sh_held[s] = 0;
         sh_budget[s] = 0;
     }
-    if (threadIdx.x == 0) sh_pool = 0;
+    if (threadIdx.x == 0) {
+        sh_pool = 0;
+        // blocks per warp of this launch: the engine's full launch or a shorter one it chose
+        const unsigned c = static_cast<unsigned>(*E.chunk_now);
+        sh_chunk = c == 0u || c > E.chunk_blocks ? E.chunk_blocks : c;
+    }
     if (threadIdx.x < 32) {
         sh_res_slot[threadIdx.x] = -1;
         sh_res_cnt[threadIdx.x] = 0;
@@ -709,9 +712,9 @@ __global__ void __launch_bounds__(T == 1 ? 640 : 256, 1) engine_chunk_kernel(Eng
     // The CTA's pool holds the last 1/kPoolDiv of the launch's blocks of every warp that has work
     // now, so a CTA whose warps are partly idle (fewer trajectories than lanes) gives its busy
     // warps as many blocks as a full CTA does, and all CTAs end together.
-    if (lane == 0 && kind >= 0) atomicAdd(&sh_pool, static_cast<int>(chunk / kPoolDiv));
+    if (lane == 0 && kind >= 0) atomicAdd(&sh_pool, static_cast<int>(sh_chunk / kPoolDiv));
     __syncthreads();
-    unsigned limit = chunk - chunk / kPoolDiv;
+    unsigned limit = sh_chunk - sh_chunk / kPoolDiv;
     while (b < limit || grant(V, limit)) {
         if (kind < 0) {
             kind = seek_work(L, E, V, n_active, cursor, b);
