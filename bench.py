@@ -254,7 +254,7 @@ def run_reference(args):
 TRAFFIC_BYTES_PER_LAUNCH = 3.64e6
 # warp instructions x 32 / lane-steps of the same capture (smsp__inst_executed): the issue bound
 # of the current kernel is 4 schedulers x 32 lanes x N_SM x f / this
-INSTRUCTIONS_PER_STEP = 22.45
+INSTRUCTIONS_PER_STEP = 22.46
 
 
 def roofline_model(n_sm: int, f_mhz: float):
